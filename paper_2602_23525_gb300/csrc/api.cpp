@@ -1,0 +1,176 @@
+// api.cpp -- the extern "C" entry points declared in include/gbfft.h.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <sstream>
+#include <string>
+
+#include "gb_plan.hpp"
+
+using namespace gb;
+
+static int copy_out(const std::string& s, char* buf, size_t len) {
+  if (buf && len > 0) {
+    const size_t k = std::min(len - 1, s.size());
+    memcpy(buf, s.data(), k);
+    buf[k] = '\0';
+  }
+  return (int)s.size();
+}
+
+extern "C" {
+
+int fft_last_error(void) { return g_last_error; }
+
+const char* fft_error_string(int code) {
+  switch (code) {
+    case FFT_OK: return "ok";
+    case FFT_ERR_INVALID_ARG: return "invalid argument";
+    case FFT_ERR_UNSUPPORTED: return "unsupported problem";
+    case FFT_ERR_ALIAS: return "input and output overlap";
+    case FFT_ERR_INPLACE_MISMATCH: return "in-place plan needs in == out and equal strides";
+    case FFT_ERR_OOM: return "device allocation failed";
+    case FFT_ERR_BUDGET: return "byte budget exceeded";
+    case FFT_ERR_CUDA: return "CUDA runtime error";
+    case FFT_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+    case FFT_ERR_WISDOM: return "wisdom missing or malformed";
+    case FFT_ERR_NO_DEVICE: return "no usable CUDA device";
+    case FFT_ERR_OUTPUT_OVERLAP: return "output map is not injective";
+    default: return "unknown error";
+  }
+}
+
+fft_plan fft_plan_dft(int rank, const fft_iodim* dims, int howmany_rank, const fft_iodim* howmany_dims, int sign,
+                      unsigned flags) {
+  Problem P;
+  int rc = canonicalize(rank, dims, howmany_rank, howmany_dims, sign, flags, P);
+  if (rc != FFT_OK) {
+    set_err(rc);
+    return nullptr;
+  }
+  if (flags & (FFT_PREC_TC_FP16 | FFT_PREC_TC_BF16 | FFT_PREC_SPLIT)) {
+    set_err(FFT_ERR_UNSUPPORTED);
+    return nullptr;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    set_err(FFT_ERR_NO_DEVICE);
+    return nullptr;
+  }
+  fft_plan p = new (std::nothrow) fft_plan_s;
+  if (!p) {
+    set_err(FFT_ERR_OOM);
+    return nullptr;
+  }
+  rc = build_plan(P, true, &p->d);
+  if (rc != FFT_OK) {
+    delete p;
+    set_err(rc);
+    return nullptr;
+  }
+  set_err(FFT_OK);
+  return p;
+}
+
+int fft_plan_explain(int rank, const fft_iodim* dims, int howmany_rank, const fft_iodim* howmany_dims, int sign,
+                     unsigned flags, char* buf, size_t len) {
+  Problem P;
+  int rc = canonicalize(rank, dims, howmany_rank, howmany_dims, sign, flags, P);
+  if (rc != FFT_OK) {
+    set_err(rc);
+    return -1;
+  }
+  P.flags |= FFT_ESTIMATE;
+  PlanData d;
+  rc = build_plan(P, false, &d);
+  if (rc != FFT_OK) {
+    set_err(rc);
+    return -1;
+  }
+  set_err(FFT_OK);
+  return copy_out(d.info, buf, len);
+}
+
+int fft_execute(fft_plan p, const void* in, void* out, void* stream) {
+  if (!p) return set_err(FFT_ERR_INVALID_ARG);
+  const int rc = execute_plan(&p->d, in, out, (cudaStream_t)stream);
+  return set_err(rc);
+}
+
+void fft_destroy(fft_plan p) {
+  if (!p) return;
+  free_plan(&p->d);
+  delete p;
+}
+
+int fft_plan_info(fft_plan p, char* buf, size_t len) {
+  if (!p) {
+    set_err(FFT_ERR_INVALID_ARG);
+    return -1;
+  }
+  return copy_out(p->d.info, buf, len);
+}
+
+double fft_plan_bytes(fft_plan p) { return p ? p->d.bytes : 0.0; }
+double fft_plan_flops(fft_plan p) { return p ? p->d.flops : 0.0; }
+int fft_plan_launches(fft_plan p) { return p ? (int)p->d.steps.size() : 0; }
+
+size_t fft_plan_scratch_bytes(fft_plan p) {
+  if (!p) return 0;
+  size_t s = 0;
+  for (size_t b : p->d.scratch_bytes) s += b;
+  return s;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- wisdom
+// Text format: a header line "gbfft-wisdom 1", then one decision per line,
+// "<canonical sub-problem key>\t<choice>".
+
+extern "C" int fft_export_wisdom(char* buf, size_t len) {
+  std::ostringstream o;
+  o << "gbfft-wisdom 1\n";
+  {
+    std::lock_guard<std::mutex> g(g_wisdom_mu);
+    for (const auto& kv : g_wisdom) o << kv.first << "\t" << kv.second << "\n";
+  }
+  set_err(FFT_OK);
+  return copy_out(o.str(), buf, len);
+}
+
+extern "C" int fft_import_wisdom(const char* text) {
+  if (!text) return set_err(FFT_ERR_INVALID_ARG);
+  std::istringstream in(text);
+  std::string line;
+  if (!std::getline(in, line) || line != "gbfft-wisdom 1") return set_err(FFT_ERR_WISDOM);
+  std::map<std::string, std::string> add;
+  while (std::getline(in, line)) {
+    if (line.empty()) continue;
+    const size_t tab = line.find('\t');
+    if (tab == std::string::npos || tab == 0 || tab + 1 >= line.size()) return set_err(FFT_ERR_WISDOM);
+    const std::string key = line.substr(0, tab), val = line.substr(tab + 1);
+    if (key.rfind("r1 ", 0) != 0) return set_err(FFT_ERR_WISDOM);
+    if (val.rfind("single:", 0) == 0) {
+      PassCfg c;
+      if (!c.parse(val.substr(7))) return set_err(FFT_ERR_WISDOM);
+    } else if (val.rfind("split:", 0) == 0) {
+      if (atoll(val.c_str() + 6) < 2) return set_err(FFT_ERR_WISDOM);
+    } else if (val.rfind("blue:", 0) == 0) {
+      if (atoll(val.c_str() + 5) < 3) return set_err(FFT_ERR_WISDOM);
+    } else {
+      return set_err(FFT_ERR_WISDOM);
+    }
+    add[key] = val;
+  }
+  for (const auto& kv : add) wisdom_put(kv.first, kv.second);
+  return set_err(FFT_OK);
+}
+
+extern "C" void fft_forget_wisdom(void) {
+  std::lock_guard<std::mutex> g(g_wisdom_mu);
+  g_wisdom.clear();
+}

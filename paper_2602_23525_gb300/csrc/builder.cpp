@@ -1,0 +1,833 @@
+// builder.cpp -- composition of algorithmic steps into a plan, and the
+// measuring planner (sec. 4.2 and 4.3 of the paper).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "gb_plan.hpp"
+
+namespace gb {
+
+static int64_t iabs64(int64_t a) { return a < 0 ? -a : a; }
+
+static int64_t prod_n(const std::vector<Dim>& V) {
+  int64_t c = 1;
+  for (const Dim& d : V) c *= d.n;
+  return c;
+}
+
+// Vector loops in canonical order: outermost first; adjacent stride runs merged.
+static std::vector<Dim> canon_vec(std::vector<Dim> V) {
+  std::vector<Dim> W;
+  for (const Dim& d : V)
+    if (d.n != 1) W.push_back(d);
+  std::stable_sort(W.begin(), W.end(), [](const Dim& a, const Dim& b) {
+    if (iabs64(a.os) != iabs64(b.os)) return iabs64(a.os) > iabs64(b.os);
+    return iabs64(a.is) > iabs64(b.is);
+  });
+  std::vector<Dim> M;
+  for (const Dim& d : W) {
+    if (!M.empty()) {
+      Dim& a = M.back();
+      if (a.is == d.n * d.is && a.os == d.n * d.os) {
+        a = {a.n * d.n, d.is, d.os};
+        continue;
+      }
+    }
+    M.push_back(d);
+  }
+  return M;
+}
+
+struct PostTw {
+  int64_t N;
+};
+
+struct Builder {
+  PlanData* P;
+  bool device;
+  bool measure;
+  bool wisdom_only;
+  std::ostringstream info;
+  std::map<int64_t, const float2*> roots_cache;
+  std::map<int64_t, std::pair<const float2*, const float2*>> split_cache;
+  std::map<std::string, std::string> forced;  // choices imposed while timing a candidate
+  int err = FFT_OK;
+
+  Builder(PlanData* p, bool dev, bool meas, bool wonly) : P(p), device(dev), measure(meas), wisdom_only(wonly) {}
+
+  void line(int depth, const std::string& s) { info << std::string(2 * depth, ' ') << s << "\n"; }
+
+  void* dalloc(size_t bytes) {
+    if (!device || err) return nullptr;
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      err = FFT_ERR_OOM;
+      return nullptr;
+    }
+    P->tables.push_back(ptr);
+    return ptr;
+  }
+
+  // tw[m] = w_n^m, m < n (sec. 6: accurate precomputed table)
+  const float2* roots(int64_t n) {
+    auto it = roots_cache.find(n);
+    if (it != roots_cache.end()) return it->second;
+    float2* t = (float2*)dalloc(sizeof(float2) * n);
+    if (t && gb_make_roots(t, n, n, 1, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+    roots_cache[n] = t;
+    return t;
+  }
+
+  // two sqrt(N) tables: lo[i] = w_N^i (i < S), hi[i] = w_N^{i S} (i <= N/S)
+  void split_roots(int64_t N, const float2** lo, const float2** hi, int64_t* S) {
+    int64_t s = (int64_t)std::ceil(std::sqrt((double)N));
+    while (s * s < N) ++s;
+    *S = s;
+    auto it = split_cache.find(N);
+    if (it != split_cache.end()) {
+      *lo = it->second.first;
+      *hi = it->second.second;
+      return;
+    }
+    const int64_t nhi = N / s + 1;
+    float2* a = (float2*)dalloc(sizeof(float2) * s);
+    float2* b = (float2*)dalloc(sizeof(float2) * nhi);
+    if (a && b) {
+      if (gb_make_roots(a, s, N, 1, 0) != cudaSuccess || gb_make_roots(b, nhi, N, s, 0) != cudaSuccess)
+        err = FFT_ERR_CUDA;
+    }
+    split_cache[N] = {a, b};
+    *lo = a;
+    *hi = b;
+  }
+
+  // device copy of a pass descriptor, owned by the plan
+  const GbPass* upload(const GbPass& p) {
+    GbPass* d = (GbPass*)dalloc(sizeof(GbPass));
+    if (d && cudaMemcpy(d, &p, sizeof(GbPass), cudaMemcpyHostToDevice) != cudaSuccess) err = FFT_ERR_CUDA;
+    return d;
+  }
+
+  int new_scratch(size_t bytes) {
+    const int id = BUF_SCRATCH0 + (int)P->scratch.size();
+    void* ptr = nullptr;
+    if (device && !err) {
+      if (cudaMalloc(&ptr, bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        err = FFT_ERR_OOM;
+        ptr = nullptr;
+      }
+    }
+    P->scratch.push_back(ptr);
+    P->scratch_bytes.push_back(bytes);
+    return id;
+  }
+
+  // ---------------------------------------------------------------- heuristics
+
+  // Estimate-mode pass configuration: coalescing first, then ~256 threads per CTA.
+  PassCfg estimate_cfg(const Dim& d, const Dim& v0, bool has_v, const std::vector<int>& rad) const {
+    PassCfg c;
+    c.radices = rad;
+    const int tpt = threads_per_transform(d.n, rad);
+    const bool in_e = iabs64(d.is) == 1, out_e = iabs64(d.os) == 1;
+    const bool in_t = has_v && iabs64(v0.is) == 1, out_t = has_v && iabs64(v0.os) == 1;
+    if (in_e && tpt >= 16) c.t_fast = 0;
+    else if (in_t) c.t_fast = 1;
+    else c.t_fast = 0;
+    c.load_mode = (c.t_fast ? in_t : (in_e && tpt >= 16)) ? GB_MOVE_DIRECT : GB_MOVE_SMEM;
+    c.store_mode = (c.t_fast ? out_t : (out_e && tpt >= 16)) ? GB_MOVE_DIRECT : GB_MOVE_SMEM;
+    c.load_copy = (!has_v || iabs64(d.is) <= iabs64(v0.is)) ? GB_COPY_ELEM_FAST : GB_COPY_T_FAST;
+    c.store_copy = (!has_v || iabs64(d.os) <= iabs64(v0.os)) ? GB_COPY_ELEM_FAST : GB_COPY_T_FAST;
+    const bool want_wide = c.t_fast || (c.load_mode == GB_MOVE_SMEM && c.load_copy == GB_COPY_T_FAST) ||
+                           (c.store_mode == GB_MOVE_SMEM && c.store_copy == GB_COPY_T_FAST);
+    int T = want_wide ? 32 : std::max(1, 256 / tpt);
+    const int64_t pitch_bytes = (int64_t)smem_pitch(d.n) * 8;
+    const int64_t soft = 96 * 1024, hard = std::min<int64_t>(smem_limit(), 200 * 1024);
+    while (T > 1 && T * tpt > 1024) T /= 2;
+    while (T > 1 && T * pitch_bytes > soft && !(want_wide && T <= 8 && T * pitch_bytes <= hard)) T /= 2;
+    while (T > 1 && T * pitch_bytes > hard) T /= 2;
+    const int64_t vn0 = has_v ? v0.n : 1;
+    while (T > 1 && T / 2 >= vn0) T /= 2;
+    c.T = std::max(1, T);
+    return c;
+  }
+
+  // n = n1 n2 for the radix-sqrt(n) step: n1 the largest codelet-smooth divisor
+  // <= sqrt(n) whose cofactor is also smooth.
+  int64_t estimate_split(int64_t n) const {
+    int64_t best = 0;
+    for (int64_t a = 2; a * a <= n; ++a)
+      if (n % a == 0 && smooth_codelet(a) && smooth_codelet(n / a) &&
+          single_pass_ok(a, default_radices(a)))
+        best = a;
+    return best;
+  }
+
+  static int64_t bluestein_length(int64_t n) {
+    int64_t m = 2 * n - 1;
+    for (;; ++m) {
+      int64_t r = m;
+      for (int p : {2, 3, 5, 7})
+        while (r % p == 0) r /= p;
+      if (r == 1) return m;
+    }
+  }
+
+  // ---------------------------------------------------------------- steps
+
+  void emit_copy(const std::vector<Dim>& V, int src, int dst, int depth) {
+    if (src == dst) {
+      for (const Dim& d : V)
+        if (d.is != d.os) {
+          err = FFT_ERR_UNSUPPORTED;  // in-place rank-0 transposes are not built
+          return;
+        }
+      line(depth, "copy in place: nothing to do");
+      return;
+    }
+    if ((int)V.size() > GB_MAX_VDIMS) {
+      err = FFT_ERR_UNSUPPORTED;
+      return;
+    }
+    Step s;
+    s.kind = STEP_COPY;
+    s.src = src;
+    s.dst = dst;
+    std::vector<Dim> W = V;
+    std::stable_sort(W.begin(), W.end(), [](const Dim& a, const Dim& b) { return iabs64(a.is) > iabs64(b.is); });
+    s.copy.nv = (int)W.size();
+    s.copy.total = 1;
+    for (int i = 0; i < (int)W.size(); ++i) {
+      s.copy.vn[i] = W[i].n;
+      s.copy.vis[i] = W[i].is;
+      s.copy.vos[i] = W[i].os;
+      s.copy.total *= W[i].n;
+    }
+    P->steps.push_back(s);
+    line(depth, "copy (rank-0) vdims=" + dims_str(W));
+  }
+
+  void emit_single(const Dim& d, const std::vector<Dim>& Vin, int src, int dst, int conj, const PassCfg& cfg,
+                   const PostTw* tw, int depth) {
+    std::vector<Dim> V = Vin;
+    if (V.empty()) V.push_back({1, 0, 0});
+    if ((int)V.size() > GB_MAX_VDIMS || (int)cfg.radices.size() > GB_MAX_STAGES) {
+      err = FFT_ERR_UNSUPPORTED;
+      return;
+    }
+    GbPass p;
+    memset(&p, 0, sizeof(p));
+    p.n = (int)d.n;
+    p.nst = (int)cfg.radices.size();
+    int64_t L = 1;
+    for (int s = 0; s < p.nst; ++s) {
+      const int R = cfg.radices[s];
+      p.radix[s] = R;
+      p.Ls[s] = (int)L;
+      p.twstep[s] = (int)(d.n / (L * R));
+      L *= R;
+    }
+    if (L != d.n) {
+      err = FFT_ERR_INVALID_ARG;
+      return;
+    }
+    p.tw = roots(d.n);
+    p.is = d.is;
+    p.os = d.os;
+    p.nv = (int)V.size();
+    for (int i = 0; i < p.nv; ++i) {
+      p.vn[i] = V[i].n;
+      p.vis[i] = V[i].is;
+      p.vos[i] = V[i].os;
+    }
+    p.tpt = threads_per_transform(d.n, cfg.radices);
+    p.T = (int)std::max<int64_t>(1, std::min<int64_t>(cfg.T, V[0].n));
+    p.t_fast = cfg.t_fast;
+    p.load_mode = cfg.load_mode;
+    p.store_mode = cfg.store_mode;
+    p.load_copy = cfg.load_copy;
+    p.store_copy = cfg.store_copy;
+    p.pitch = smem_pitch(d.n);
+    p.tiles0 = (V[0].n + p.T - 1) / p.T;
+    p.ntiles = p.tiles0;
+    for (int i = 1; i < p.nv; ++i) p.ntiles *= V[i].n;
+    p.conj = conj;
+    if (tw) {
+      p.post_tw = 1;
+      p.twN = tw->N;
+      split_roots(tw->N, &p.tw_lo, &p.tw_hi, &p.twS);
+    }
+    p.status = P->d_status;
+    Step s;
+    s.kind = STEP_PASS;
+    s.pass = p;
+    s.dpass = upload(p);
+    s.src = src;
+    s.dst = dst;
+    s.threads = p.T * p.tpt;
+    const bool no_smem = p.nst == 1 && p.load_mode == GB_MOVE_DIRECT && p.store_mode == GB_MOVE_DIRECT;
+    s.smem = no_smem ? 0 : (size_t)p.T * p.pitch * sizeof(float2);
+    if (s.threads > 1024 || (int64_t)s.smem > smem_limit()) {
+      err = FFT_ERR_UNSUPPORTED;
+      return;
+    }
+    P->steps.push_back(s);
+    std::ostringstream o;
+    o << "pass stockham n=" << d.n << " is=" << d.is << " os=" << d.os << " cfg=" << cfg.str()
+      << " tpt=" << p.tpt << " threads=" << s.threads << " smem=" << s.smem << " tiles=" << p.ntiles
+      << " vdims=" << dims_str(V);
+    if (tw) o << " post-twiddle w_" << tw->N << "^(v0*k)";
+    if (conj) o << " conj";
+    line(depth, o.str());
+  }
+
+  void emit_fourstep(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t n1,
+                     int depth) {
+    const int64_t n = d.n, n2 = n / n1;
+    std::ostringstream o;
+    o << "cooley-tukey n=" << n << " = " << n1 << " x " << n2 << " (radix-" << n1 << " step, eq. 2)";
+    line(depth, o.str());
+    const int64_t count = prod_n(V);
+    const int S = new_scratch((size_t)count * n * sizeof(float2));
+    // scratch layout: [vector index][k1][l2]
+    std::vector<Dim> Vs(V.size());
+    int64_t st = n;
+    for (int i = (int)V.size() - 1; i >= 0; --i) {
+      Vs[i] = {V[i].n, V[i].is, st};
+      st *= V[i].n;
+    }
+    // pass 1: n2 DFTs of size n1 over l1 (input stride n2 is), twiddle w_n^{l2 k1}
+    std::vector<Dim> V1;
+    V1.push_back({n2, d.is, 1});
+    for (const Dim& v : Vs) V1.push_back(v);
+    const Dim d1{n1, n2 * d.is, n2};
+    PassCfg c1 = estimate_cfg(d1, V1[0], true, default_radices(n1));
+    PostTw tw{n};
+    emit_single(d1, V1, src, S, conj, c1, &tw, depth + 1);
+    // sub-problem: n1 DFTs of size n2 over l2, output Y[k1 + k2 n1]
+    std::vector<Dim> V2;
+    V2.push_back({n1, n2, d.os});
+    int64_t st2 = n;
+    for (int i = (int)V.size() - 1; i >= 0; --i) {
+      V2.push_back({V[i].n, st2, V[i].os});
+      st2 *= V[i].n;
+    }
+    solve_rank1({n2, 1, n1 * d.os}, V2, S, dst, conj, depth + 1);
+  }
+
+  void emit_bluestein(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t m,
+                      int depth) {
+    const int64_t n = d.n;
+    std::vector<int> rad = default_radices(m);
+    std::ostringstream o;
+    o << "bluestein n=" << n << " m=" << m << " (chirp-z, prime-size plan)";
+    line(depth, o.str());
+    float2* w = (float2*)dalloc(sizeof(float2) * n);
+    float2* B = (float2*)dalloc(sizeof(float2) * m);
+    if (device && !err) {
+      double2* work = nullptr;
+      if (cudaMalloc(&work, sizeof(double2) * 2 * m) != cudaSuccess) {
+        cudaGetLastError();
+        err = FFT_ERR_OOM;
+        return;
+      }
+      if (gb_make_chirp(w, n, 0) != cudaSuccess ||
+          gb_make_bluestein_kernel(B, n, m, rad.data(), (int)rad.size(), work, 0) != cudaSuccess ||
+          cudaDeviceSynchronize() != cudaSuccess)
+        err = FFT_ERR_CUDA;
+      cudaFree(work);
+    }
+    std::vector<Dim> VV = V;
+    if (VV.empty()) VV.push_back({1, 0, 0});
+    const bool fused = single_pass_ok(m, rad) && (int)VV.size() <= GB_MAX_VDIMS;
+    if (fused) {
+      GbPass p;
+      memset(&p, 0, sizeof(p));
+      p.n = (int)m;
+      p.nst = (int)rad.size();
+      int64_t L = 1;
+      for (int s = 0; s < p.nst; ++s) {
+        p.radix[s] = rad[s];
+        p.Ls[s] = (int)L;
+        p.twstep[s] = (int)(m / (L * rad[s]));
+        L *= rad[s];
+      }
+      p.tw = roots(m);
+      p.is = d.is;
+      p.os = d.os;
+      p.nv = (int)VV.size();
+      for (int i = 0; i < p.nv; ++i) {
+        p.vn[i] = VV[i].n;
+        p.vis[i] = VV[i].is;
+        p.vos[i] = VV[i].os;
+      }
+      p.tpt = threads_per_transform(m, rad);
+      p.T = 1;
+      p.pitch = smem_pitch(m);
+      p.load_mode = p.store_mode = GB_MOVE_SMEM;
+      p.tiles0 = VV[0].n;
+      p.ntiles = prod_n(VV);
+      p.conj = conj;
+      p.blue = 1;
+      p.bn = (int)n;
+      p.bw = w;
+      p.bB = B;
+      p.status = P->d_status;
+      Step s;
+      s.kind = STEP_PASS;
+      s.pass = p;
+      s.dpass = upload(p);
+      s.src = src;
+      s.dst = dst;
+      s.threads = p.tpt;
+      s.smem = (size_t)p.pitch * sizeof(float2);
+      P->steps.push_back(s);
+      std::ostringstream q;
+      q << "pass bluestein-fused m=" << m << " radices=" << PassCfg{rad}.str() << " threads=" << s.threads
+        << " smem=" << s.smem << " vdims=" << dims_str(VV);
+      line(depth + 1, q.str());
+      return;
+    }
+    if ((int)V.size() > GB_MAX_VDIMS) {
+      err = FFT_ERR_UNSUPPORTED;
+      return;
+    }
+    const int64_t count = prod_n(V);
+    const int S0 = new_scratch((size_t)count * m * sizeof(float2));
+    const int S1 = new_scratch((size_t)count * m * sizeof(float2));
+    GbBlueIO b;
+    memset(&b, 0, sizeof(b));
+    b.n = n;
+    b.m = m;
+    b.is = d.is;
+    b.os = d.os;
+    b.nv = (int)V.size();
+    for (int i = 0; i < b.nv; ++i) {
+      b.vn[i] = V[i].n;
+      b.vis[i] = V[i].is;
+      b.vos[i] = V[i].os;
+    }
+    b.count = count;
+    b.w = w;
+    b.B = B;
+    b.conj = conj;
+    Step pre;
+    pre.kind = STEP_BLUE_PRE;
+    pre.blue = b;
+    pre.src = src;
+    pre.dst = S0;
+    P->steps.push_back(pre);
+    line(depth + 1, "pointwise a = pad(x w)");
+    solve_rank1({m, 1, 1}, {{count, m, m}}, S0, S1, 0, depth + 1);
+    Step mul;
+    mul.kind = STEP_BLUE_MUL;
+    mul.blue = b;
+    mul.src = S1;
+    mul.dst = S1;
+    P->steps.push_back(mul);
+    line(depth + 1, "pointwise Z = conj(A Bhat)");
+    solve_rank1({m, 1, 1}, {{count, m, m}}, S1, S0, 0, depth + 1);
+    Step post;
+    post.kind = STEP_BLUE_POST;
+    post.blue = b;
+    post.src = S0;
+    post.dst = dst;
+    P->steps.push_back(post);
+    line(depth + 1, "pointwise Y = w conj(D)");
+  }
+
+  // ---------------------------------------------------------------- planner
+
+  static std::string key_rank1(const Dim& d, const std::vector<Dim>& V, bool inplace) {
+    std::ostringstream o;
+    o << "r1 n=" << d.n << " is=" << d.is << " os=" << d.os << " v=" << dims_str(V) << " ip=" << (inplace ? 1 : 0);
+    return o.str();
+  }
+
+  std::vector<std::string> candidates(const Dim& d, const std::vector<Dim>& V) {
+    std::vector<std::string> c;
+    const int64_t n = d.n;
+    Dim v0{1, 0, 0};
+    bool has_v = false;
+    if (!V.empty()) {
+      v0 = V[tile_dim(V)];
+      has_v = true;
+    }
+    if (smooth_codelet(n)) {
+      std::vector<int> rad = default_radices(n);
+      if (single_pass_ok(n, rad)) {
+        PassCfg base = estimate_cfg(d, v0, has_v, rad);
+        c.push_back("single:" + base.str());
+        if (measure) {
+          // radix order reversed
+          std::vector<int> rr(rad.rbegin(), rad.rend());
+          if (rr != rad) {
+            PassCfg x = base;
+            x.radices = rr;
+            c.push_back("single:" + x.str());
+          }
+          // 16 -> 4 x 4 where it keeps the thread count legal
+          std::vector<int> r4;
+          for (int R : rad) {
+            if (R == 16) {
+              r4.push_back(4);
+              r4.push_back(4);
+            } else r4.push_back(R);
+          }
+          if (r4 != rad && (int)r4.size() <= GB_MAX_STAGES && threads_per_transform(n, r4) <= 1024) {
+            PassCfg x = estimate_cfg(d, v0, has_v, r4);
+            c.push_back("single:" + x.str());
+          }
+          for (int f : {2, -2}) {
+            PassCfg x = base;
+            x.T = f > 0 ? base.T * 2 : std::max(1, base.T / 2);
+            const int tpt = threads_per_transform(n, rad);
+            if (x.T != base.T && x.T * tpt <= 1024 && x.T * (int64_t)smem_pitch(n) * 8 <= smem_limit())
+              c.push_back("single:" + x.str());
+          }
+          if (base.load_mode == GB_MOVE_DIRECT || base.store_mode == GB_MOVE_DIRECT) {
+            PassCfg x = base;
+            x.load_mode = x.store_mode = GB_MOVE_SMEM;
+            c.push_back("single:" + x.str());
+          }
+        }
+      }
+      if (n > 64) {
+        const int64_t a = estimate_split(n);
+        if (a > 1) {
+          c.push_back("split:" + std::to_string(a));
+          if (measure) {
+            for (int64_t b : {(int64_t)16, (int64_t)64, (int64_t)256, (int64_t)1024}) {
+              if (b != a && n % b == 0 && n / b > 1 && smooth_codelet(n / b) && b * b <= n * 4)
+                c.push_back("split:" + std::to_string(b));
+            }
+          }
+        }
+      }
+    }
+    if (!smooth_codelet(n) || c.empty()) c.push_back("blue:" + std::to_string(bluestein_length(n)));
+    return c;
+  }
+
+  static int tile_dim(const std::vector<Dim>& V) {
+    int best = 0;
+    for (int i = 1; i < (int)V.size(); ++i) {
+      const int64_t a = std::min(iabs64(V[i].is), iabs64(V[i].os)), b = std::min(iabs64(V[best].is), iabs64(V[best].os));
+      const int64_t sa = iabs64(V[i].is) + iabs64(V[i].os), sb = iabs64(V[best].is) + iabs64(V[best].os);
+      if (a < b || (a == b && sa < sb)) best = i;
+    }
+    return best;
+  }
+
+  // vector loops for a pass: tile dim first, then outermost .. innermost
+  static std::vector<Dim> order_for_pass(const std::vector<Dim>& V) {
+    if (V.empty()) return V;
+    const int t = tile_dim(V);
+    std::vector<Dim> rest;
+    for (int i = 0; i < (int)V.size(); ++i)
+      if (i != t) rest.push_back(V[i]);
+    std::stable_sort(rest.begin(), rest.end(), [](const Dim& a, const Dim& b) { return iabs64(a.is) > iabs64(b.is); });
+    std::vector<Dim> out;
+    out.push_back(V[t]);
+    out.insert(out.end(), rest.begin(), rest.end());
+    return out;
+  }
+
+  double time_choice(const Dim& d, const std::vector<Dim>& V, bool inplace, const std::string& key,
+                     const std::string& choice);
+
+  std::string choose(const Dim& d, const std::vector<Dim>& V, bool inplace) {
+    const std::string key = key_rank1(d, V, inplace);
+    auto f = forced.find(key);
+    if (f != forced.end()) return f->second;
+    std::string val;
+    if (wisdom_get(key, &val)) return val;
+    if (wisdom_only) {
+      err = FFT_ERR_WISDOM;
+      return "";
+    }
+    std::vector<std::string> cands = candidates(d, V);
+    if (!measure || !device || cands.size() == 1) {
+      if (measure && device) wisdom_put(key, cands[0]);
+      return cands[0];
+    }
+    double best = 1e30;
+    std::string pick = cands[0];
+    for (const std::string& c : cands) {
+      const double t = time_choice(d, V, inplace, key, c);
+      if (t > 0 && t < best) {
+        best = t;
+        pick = c;
+      }
+    }
+    wisdom_put(key, pick);
+    return pick;
+  }
+
+  void solve_rank1(const Dim& d, const std::vector<Dim>& Vraw, int src, int dst, int conj, int depth) {
+    if (err) return;
+    std::vector<Dim> V = canon_vec(Vraw);
+    if (d.n == 1) {
+      std::vector<Dim> W = V;
+      W.push_back({1, d.is, d.os});
+      emit_copy(canon_vec(W), src, dst, depth);
+      return;
+    }
+    const std::string choice = choose(d, V, src == dst);
+    if (err) return;
+    if (choice.rfind("single:", 0) == 0) {
+      PassCfg cfg;
+      if (!cfg.parse(choice.substr(7))) {
+        err = FFT_ERR_WISDOM;
+        return;
+      }
+      emit_single(d, order_for_pass(V), src, dst, conj, cfg, nullptr, depth);
+    } else if (choice.rfind("split:", 0) == 0) {
+      const int64_t n1 = atoll(choice.c_str() + 6);
+      if (n1 < 2 || d.n % n1 != 0) {
+        err = FFT_ERR_WISDOM;
+        return;
+      }
+      emit_fourstep(d, V, src, dst, conj, n1, depth);
+    } else if (choice.rfind("blue:", 0) == 0) {
+      const int64_t m = atoll(choice.c_str() + 5);
+      if (m < 2 * d.n - 1) {
+        err = FFT_ERR_WISDOM;
+        return;
+      }
+      emit_bluestein(d, V, src, dst, conj, m, depth);
+    } else {
+      err = FFT_ERR_WISDOM;
+    }
+  }
+
+  // separable multi-dimensional DFT: one rank-1 sub-problem per dimension
+  void solve(const std::vector<Dim>& N, const std::vector<Dim>& V, int src, int dst, int conj, int depth) {
+    if (N.empty()) {
+      emit_copy(V, src, dst, depth);
+      return;
+    }
+    if (N.size() == 1) {
+      solve_rank1(N[0], V, src, dst, conj, depth);
+      return;
+    }
+    std::vector<int> order(N.size());
+    for (size_t i = 0; i < N.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return iabs64(N[a].is) < iabs64(N[b].is); });
+    line(depth, "separable rank-" + std::to_string(N.size()) + " DFT, one pass group per dimension");
+    for (size_t k = 0; k < order.size(); ++k) {
+      const int a = order[k];
+      std::vector<Dim> others;
+      if (k == 0) {
+        for (size_t b = 0; b < N.size(); ++b)
+          if ((int)b != a) others.push_back(N[b]);
+        others.insert(others.end(), V.begin(), V.end());
+        solve_rank1(N[a], others, src, dst, conj, depth + 1);
+      } else {
+        for (size_t b = 0; b < N.size(); ++b)
+          if ((int)b != a) others.push_back({N[b].n, N[b].os, N[b].os});
+        for (const Dim& v : V) others.push_back({v.n, v.os, v.os});
+        solve_rank1({N[a].n, N[a].os, N[a].os}, others, dst, dst, conj, depth + 1);
+      }
+      if (err) return;
+    }
+  }
+};
+
+static void release(PlanData* p) {
+  for (void* t : p->tables)
+    if (t) cudaFree(t);
+  for (void* s : p->scratch)
+    if (s) cudaFree(s);
+  if (p->d_status) cudaFree(p->d_status);
+  p->tables.clear();
+  p->scratch.clear();
+  p->scratch_bytes.clear();
+  p->d_status = nullptr;
+}
+
+void free_plan(PlanData* p) { release(p); }
+
+int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  switch (s.kind) {
+    case STEP_PASS: {
+      e = gb_launch_pass(s.pass, s.dpass, bufs[s.src], bufs[s.dst], s.threads, s.smem, s.grid, st);
+      break;
+    }
+    case STEP_COPY: {
+      GbCopy c = s.copy;
+      c.in = bufs[s.src];
+      c.out = bufs[s.dst];
+      e = gb_launch_copy(c, st);
+      break;
+    }
+    case STEP_BLUE_PRE: {
+      GbBlueIO b = s.blue;
+      b.in = bufs[s.src];
+      b.work = bufs[s.dst];
+      e = gb_launch_blue_pre(b, st);
+      break;
+    }
+    case STEP_BLUE_MUL: {
+      e = gb_launch_blue_mul(s.blue, bufs[s.dst], st);
+      break;
+    }
+    case STEP_BLUE_POST: {
+      GbBlueIO b = s.blue;
+      b.out = bufs[s.dst];
+      e = gb_launch_blue_post(b, bufs[s.src], st);
+      break;
+    }
+    default:
+      return FFT_ERR_INVALID_ARG;
+  }
+  return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
+}
+
+static int run_steps(PlanData* p, const void* in, void* out, cudaStream_t st) {
+  std::vector<float2*> bufs(BUF_SCRATCH0 + p->scratch.size());
+  bufs[BUF_IN] = (float2*)in;
+  bufs[BUF_OUT] = (float2*)out;
+  for (size_t k = 0; k < p->scratch.size(); ++k) bufs[BUF_SCRATCH0 + k] = (float2*)p->scratch[k];
+  for (const Step& s : p->steps) {
+    const int rc = launch_step(s, bufs.data(), st);
+    if (rc != FFT_OK) return rc;
+  }
+  return FFT_OK;
+}
+
+// Time one candidate for a rank-1 sub-problem: best of 3 after a warm-up,
+// on planner-owned buffers sized like the sub-problem (the outermost loop is
+// shortened when the footprint exceeds 1 GiB).
+double Builder::time_choice(const Dim& d, const std::vector<Dim>& Vin, bool inplace, const std::string& key,
+                            const std::string& choice) {
+  std::vector<Dim> V = Vin;
+  std::vector<Dim> N1{d};
+  const int64_t cap = (int64_t)1 << 27;  // elements per buffer
+  for (int guard = 0; guard < 64; ++guard) {
+    int64_t a, b, c, e;
+    footprint(N1, V, true, &a, &b);
+    footprint(N1, V, false, &c, &e);
+    if (b - a + 1 <= cap && e - c + 1 <= cap) break;
+    int big = -1;
+    for (int i = 0; i < (int)V.size(); ++i)
+      if (V[i].n > 1 && (big < 0 || iabs64(V[i].is) > iabs64(V[big].is))) big = i;
+    if (big < 0) return -1;
+    V[big].n = (V[big].n + 1) / 2;
+  }
+  PlanData tmp;
+  if (cudaMalloc(&tmp.d_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  cudaMemset(tmp.d_status, 0, sizeof(int));
+  Builder b(&tmp, true, true, false);
+  b.forced = forced;
+  b.forced[key] = choice;
+  b.forced[key_rank1(d, canon_vec(V), inplace)] = choice;
+  b.solve_rank1(d, V, 0, inplace ? 0 : 1, 0, 0);
+  double best = -1;
+  int64_t ilo, ihi, olo, ohi;
+  footprint(N1, V, true, &ilo, &ihi);
+  footprint(N1, V, false, &olo, &ohi);
+  float2 *ib = nullptr, *ob = nullptr;
+  if (!b.err && cudaMalloc(&ib, sizeof(float2) * (ihi - ilo + 1)) == cudaSuccess &&
+      (inplace || cudaMalloc(&ob, sizeof(float2) * (ohi - olo + 1)) == cudaSuccess)) {
+    cudaMemset(ib, 0, sizeof(float2) * (ihi - ilo + 1));
+    if (ob) cudaMemset(ob, 0, sizeof(float2) * (ohi - olo + 1));
+    float2* in0 = ib - ilo;
+    float2* out0 = inplace ? in0 : ob - olo;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    bool ok = run_steps(&tmp, in0, out0, 0) == FFT_OK && cudaDeviceSynchronize() == cudaSuccess;
+    for (int rep = 0; ok && rep < 3; ++rep) {
+      cudaEventRecord(e0, 0);
+      ok = run_steps(&tmp, in0, out0, 0) == FFT_OK;
+      cudaEventRecord(e1, 0);
+      if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0 || ms < best) best = ms;
+      } else ok = false;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  cudaGetLastError();
+  if (ib) cudaFree(ib);
+  if (ob) cudaFree(ob);
+  release(&tmp);
+  // decisions for nested sub-problems made while timing stay in the memo
+  return best;
+}
+
+int build_plan(const Problem& P, bool device, PlanData* out) {
+  out->prob = P;
+  out->inplace = (P.flags & FFT_INPLACE) != 0;
+  std::ostringstream head;
+  head << "dft rank=" << P.N.size() << " n=" << dims_str(P.N) << " howmany=" << dims_str(P.V)
+       << " sign=" << P.sign << (out->inplace ? " in-place" : "") << ((P.flags & FFT_ESTIMATE) ? " estimate" : "")
+       << "\n";
+  if (P.empty) {
+    out->info = head.str() + "  empty problem: no-op\n";
+    return FFT_OK;
+  }
+  footprint(P.N, P.V, true, &out->in_lo, &out->in_hi);
+  footprint(P.N, P.V, false, &out->out_lo, &out->out_hi);
+  int64_t pts = 1, count = 1;
+  for (const Dim& d : P.N) pts *= d.n;
+  for (const Dim& d : P.V) count *= d.n;
+  out->bytes = 16.0 * (double)pts * (double)count;
+  out->flops = pts > 1 ? 5.0 * (double)pts * std::log2((double)pts) * (double)count : 0.0;
+  if (device) {
+    if (cudaGetDevice(&out->device) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT_ERR_NO_DEVICE;
+    }
+    if (cudaMalloc(&out->d_status, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return FFT_ERR_OOM;
+    }
+    cudaMemset(out->d_status, 0, sizeof(int));
+  }
+  const bool measure = device && !(P.flags & FFT_ESTIMATE);
+  Builder b(out, device, measure, (P.flags & FFT_WISDOM_ONLY) != 0);
+  const int conj = P.sign > 0 ? 1 : 0;
+  b.solve(P.N, P.V, BUF_IN, out->inplace ? BUF_IN : BUF_OUT, conj, 1);
+  if (!b.err && device && cudaDeviceSynchronize() != cudaSuccess) b.err = FFT_ERR_CUDA;
+  out->info = head.str() + b.info.str();
+  if (b.err) {
+    release(out);
+    return b.err;
+  }
+  return FFT_OK;
+}
+
+int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st) {
+  if (p->prob.empty) return FFT_OK;
+  if (!in || !out) return FFT_ERR_INVALID_ARG;
+  if (p->inplace) {
+    if (in != out) return FFT_ERR_INPLACE_MISMATCH;
+  } else {
+    const char* a0 = (const char*)in + 8 * p->in_lo;
+    const char* a1 = (const char*)in + 8 * (p->in_hi + 1);
+    const char* b0 = (const char*)out + 8 * p->out_lo;
+    const char* b1 = (const char*)out + 8 * (p->out_hi + 1);
+    if (a0 < b1 && b0 < a1) return FFT_ERR_ALIAS;
+  }
+  return run_steps(p, in, p->inplace ? (void*)in : out, st);
+}
+
+}  // namespace gb

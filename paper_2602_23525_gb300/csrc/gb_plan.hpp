@@ -1,0 +1,100 @@
+// gb_plan.hpp -- internal host-side structures of problems and plans.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gbfft.h"
+#include "gb_kernels.h"
+#include "gb_pass.h"
+
+namespace gb {
+
+// An I/O dimension (n, is, os) of sec. 4.1, strides in complex elements.
+struct Dim {
+  int64_t n, is, os;
+};
+
+// A canonical problem dft(N, V, I, O) without its pointers.
+struct Problem {
+  std::vector<Dim> N, V;
+  int sign = -1;
+  unsigned flags = 0;
+  bool empty = false;
+};
+
+// Configuration of one Stockham pass (the choices the planner makes).
+struct PassCfg {
+  std::vector<int> radices;
+  int T = 1, t_fast = 0, load_mode = 0, store_mode = 0, load_copy = 0, store_copy = 0;
+  std::string str() const;
+  bool parse(const std::string& s);
+};
+
+enum StepKind { STEP_PASS = 0, STEP_COPY = 1, STEP_BLUE_PRE = 2, STEP_BLUE_MUL = 3, STEP_BLUE_POST = 4 };
+
+// Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.
+enum { BUF_IN = 0, BUF_OUT = 1, BUF_SCRATCH0 = 2 };
+
+struct Step {
+  int kind = STEP_PASS;
+  GbPass pass{};
+  const GbPass* dpass = nullptr;  // device copy of pass (what the kernel reads)
+  GbCopy copy{};
+  GbBlueIO blue{};
+  int src = BUF_IN, dst = BUF_OUT;
+  int threads = 0;
+  size_t smem = 0;
+  int64_t grid = 0;
+};
+
+struct PlanData {
+  Problem prob;
+  std::vector<Step> steps;
+  std::vector<void*> tables;   // device memory owned by the plan
+  std::vector<void*> scratch;  // scratch buffers (ids BUF_SCRATCH0 + k)
+  std::vector<size_t> scratch_bytes;
+  int* d_status = nullptr;
+  std::string info;
+  double bytes = 0.0, flops = 0.0;
+  int64_t in_lo = 0, in_hi = 0, out_lo = 0, out_hi = 0;
+  bool inplace = false;
+  int device = -1;
+};
+
+// plan.cpp
+extern thread_local int g_last_error;
+int set_err(int e);
+int canonicalize(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, int sign, unsigned flags,
+                 Problem& P);
+void footprint(const std::vector<Dim>& N, const std::vector<Dim>& V, bool input, int64_t* lo, int64_t* hi);
+std::string dims_str(const std::vector<Dim>& v);
+bool smooth_codelet(int64_t n);
+int64_t largest_prime_factor(int64_t n);
+std::vector<int> default_radices(int64_t n);
+int threads_per_transform(int64_t n, const std::vector<int>& rad);
+int smem_pitch(int64_t n);
+int smem_limit();
+bool single_pass_ok(int64_t n, const std::vector<int>& rad);
+extern std::mutex g_wisdom_mu;
+extern std::map<std::string, std::string> g_wisdom;
+bool wisdom_get(const std::string& key, std::string* val);
+void wisdom_put(const std::string& key, const std::string& val);
+
+// builder.cpp
+// Build the steps of a plan.  device = false builds the estimate-mode plan
+// text only (no allocation, no timing).  Returns an FFT_* code.
+int build_plan(const Problem& P, bool device, PlanData* out);
+void free_plan(PlanData* p);
+int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st);
+int launch_step(const Step& s, float2* const* bufs, cudaStream_t st);
+
+}  // namespace gb
+
+struct fft_plan_s {
+  gb::PlanData d;
+};

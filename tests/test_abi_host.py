@@ -1,0 +1,177 @@
+"""The C-ABI library on the host: it loads, exports every entry point declared in
+include/gbfft.h, and its host logic (problem canonicalisation and validation,
+plan construction in estimate mode) behaves as documented.  No GPU needed:
+fft_plan_explain builds the plan text without touching a device.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import __graft_entry__
+from paper_2602_23525_gb300 import gbfft
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbfft.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(fft_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_core_entry_points():
+    names = declared_functions()
+    for n in ("fft_plan_dft", "fft_execute", "fft_destroy", "fft_last_error", "fft_error_string",
+              "fft_plan_info", "fft_export_wisdom", "fft_import_wisdom"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(gbfft.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", gbfft.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fft_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_covers_header():
+    assert set(declared_functions()) <= set(gbfft._SIGNATURES)
+
+
+def test_error_strings():
+    assert gbfft.fft_error_string(0) == "ok"
+    for code in range(1, 12):
+        assert gbfft.fft_error_string(code) not in ("ok", "unknown error")
+    assert gbfft.fft_error_string(999) == "unknown error"
+
+
+def explain(dims, howmany=(), sign=-1, flags=0):
+    return gbfft.fft_plan_explain(dims, howmany, sign, flags)
+
+
+def explain_err(dims, howmany=(), sign=-1, flags=0):
+    with pytest.raises(gbfft.GbfftError) as e:
+        explain(dims, howmany, sign, flags)
+    return e.value.code
+
+
+# ---------------------------------------------------------------- validation
+
+def test_invalid_arguments():
+    assert explain_err([(8, 1, 1)], sign=0) == gbfft.FFT_ERR_INVALID_ARG
+    assert explain_err([(8, 1, 1)], sign=2) == gbfft.FFT_ERR_INVALID_ARG
+    assert explain_err([(-1, 1, 1)]) == gbfft.FFT_ERR_INVALID_ARG
+    assert explain_err([(8, 1, 1)], [(-3, 8, 8)]) == gbfft.FFT_ERR_INVALID_ARG
+    assert explain_err([(8, 1, 1)], flags=1 << 20) == gbfft.FFT_ERR_INVALID_ARG
+    assert explain_err([(2, 1, 1)] * 4) == gbfft.FFT_ERR_UNSUPPORTED
+
+
+def test_output_overlap_rejected():
+    # zero output stride with n > 1
+    assert explain_err([(8, 1, 0)]) == gbfft.FFT_ERR_OUTPUT_OVERLAP
+    # vector stride smaller than the transform's span
+    assert explain_err([(8, 1, 1)], [(4, 8, 4)]) == gbfft.FFT_ERR_OUTPUT_OVERLAP
+    # zero input stride is a broadcast and is allowed
+    assert "pass" in explain([(8, 0, 1)])
+
+
+def test_inplace_requires_equal_strides():
+    assert explain_err([(8, 1, 2)], flags=gbfft.FFT_INPLACE) == gbfft.FFT_ERR_INPLACE_MISMATCH
+    assert "in-place" in explain([(8, 1, 1)], [(4, 8, 8)], flags=gbfft.FFT_INPLACE)
+
+
+def test_empty_problem_is_noop():
+    assert "no-op" in explain([(0, 1, 1)])
+    assert "no-op" in explain([(16, 1, 1)], [(0, 16, 16)])
+
+
+def test_length_one_dims_dropped_and_runs_merged():
+    t = explain([(64, 1, 1), (1, 5, 7)], [(4, 64 * 3, 64 * 3), (3, 64, 64), (1, 9, 9)])
+    assert "n=[(64,1,1)]" in t
+    assert "howmany=[(12,64,64)]" in t
+
+
+def test_rank0_is_a_copy():
+    t = explain([], [(10, 1, 1)])
+    assert "copy" in t
+
+
+# ---------------------------------------------------------------- plan structure
+
+def test_plan_single_pass_pow2():
+    t = explain([(4096, 1, 1)], [(64, 4096, 4096)])
+    assert "pass stockham n=4096" in t and "R=16.16.16" in t and "cooley-tukey" not in t
+
+
+def test_plan_mixed_radix():
+    t = explain([(1000, 1, 1)], [(512, 1000, 1000)])
+    assert "pass stockham n=1000" in t
+    assert "R=8.5.5.5" in t
+    assert "R=9.9.9.3" in explain([(2187, 512, 1)], [(512, 1, 2187)])
+
+
+def test_plan_large_is_multi_pass():
+    t = explain([(2 ** 24, 1, 1)])
+    assert "cooley-tukey n=16777216 = 4096 x 4096" in t
+    assert t.count("pass stockham") == 2
+    assert "post-twiddle" in t
+
+
+def test_plan_prime_is_bluestein():
+    t = explain([(10007, 1, 1)], [(512, 10007, 10007)])
+    assert "bluestein n=10007" in t
+    t = explain([(97, 1, 1)])
+    assert "bluestein n=97" in t and "bluestein-fused" in t
+
+
+def test_plan_multidim_separable():
+    t = explain([(4096, 4096, 4096), (4096, 1, 1)])
+    assert "separable rank-2" in t
+    assert t.count("pass stockham n=4096") == 2
+
+
+def test_size30_radix_decomposition():
+    """Fig. 3 of the paper decomposes a size-30 DFT with radices 3, 2 and 5; the
+    planner's codelet stages cover the same factors."""
+    t = explain([(30, 1, 1)])
+    m = re.search(r"R=([0-9.]+)", t)
+    assert m and sorted(int(r) for r in m.group(1).split(".")) == [2, 3, 5]
+
+
+def test_explain_is_deterministic():
+    a = explain([(7168, 1, 1)], [(512, 7168, 7168)])
+    b = explain([(7168, 1, 1)], [(512, 7168, 7168)])
+    assert a == b
+
+
+def test_wisdom_text_roundtrip_and_rejection():
+    gbfft.fft_forget_wisdom()
+    good = "gbfft-wisdom 1\nr1 n=64 is=1 os=1 v=[] ip=0\tsingle:R=16.4:T=4:f=0:l=1:s=1:lc=0:sc=0\n"
+    gbfft.fft_import_wisdom(good)
+    assert "single:R=16.4" in gbfft.fft_export_wisdom()
+    for bad in ("nonsense", "gbfft-wisdom 1\nr1 x\tsingle:R=6\n", "gbfft-wisdom 1\nfoo\tbar\n"):
+        with pytest.raises(gbfft.GbfftError) as e:
+            gbfft.fft_import_wisdom(bad)
+        assert e.value.code == gbfft.FFT_ERR_WISDOM
+    gbfft.fft_forget_wisdom()
+    assert gbfft.fft_export_wisdom().strip() == "gbfft-wisdom 1"
+
+
+def test_wisdom_decides_estimate_plan():
+    gbfft.fft_forget_wisdom()
+    key = "r1 n=64 is=1 os=1 v=[] ip=0"
+    gbfft.fft_import_wisdom(f"gbfft-wisdom 1\n{key}\tsingle:R=4.4.4:T=1:f=0:l=1:s=1:lc=0:sc=0\n")
+    assert "R=4.4.4" in explain([(64, 1, 1)])
+    gbfft.fft_forget_wisdom()
+    assert "R=16.4" in explain([(64, 1, 1)])

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Every case compares each transform's output with the oracle (relative L2
+<= 2e-6, the FP32 tolerance of the workload definition); copies and
+repeated runs must be bit-exact.  Sizes are chosen so the oracle finishes in
+seconds while spanning several CTA tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import fft_inputs
+from parity import TOL, check, reference, run_gpu, per_transform_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2602_23525_gb300 import gbfft  # noqa: E402
+
+EST = gbfft.FFT_ESTIMATE
+
+
+def u(count, seed):
+    return fft_inputs.uniform_c64(count, seed)
+
+
+# ---------------------------------------------------------------- the small workload
+
+@pytest.mark.parametrize("flags", [EST, gbfft.FFT_MEASURE])
+def test_config1_n4096_batch64_forward(flags):
+    n, b = 4096, 64
+    x = u(n * b, fft_inputs.seed_for(0))
+    err, info = check([(n, 1, 1)], [(b, n, n)], -1, x, flags=flags)
+    print(f"config-1 max rel-L2 {err:.3e}\n{info}")
+
+
+# ---------------------------------------------------------------- sizes
+
+@pytest.mark.parametrize("e", range(0, 21))
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_pow2_sizes(e, sign):
+    n = 2 ** e
+    b = max(1, min(2 ** 18 // n, 64)) + (3 if n <= 4096 else 0)  # ragged batch for small n
+    x = u(n * b, fft_inputs.seed_for(1, e))
+    check([(n, 1, 1)], [(b, n, n)], sign, x, flags=EST, algo="ct" if n > 4096 else "auto")
+
+
+@pytest.mark.parametrize("n", [3, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15, 18, 20, 21, 25, 27, 30, 35, 36, 45, 49,
+                               60, 63, 77, 81, 99, 100, 121, 125, 143, 169, 243, 343, 360, 625, 1000,
+                               1001, 2187, 3125, 3600, 3840, 7168, 10000, 15625])
+def test_mixed_radix_sizes(n):
+    b = max(1, 2 ** 15 // n) + 1
+    x = fft_inputs.gaussian_c64(n * b, n)
+    check([(n, 1, 1)], [(b, n, n)], -1, x, flags=EST)
+
+
+@pytest.mark.parametrize("n", [17, 19, 23, 29, 31, 37, 61, 67, 97, 127, 257, 1009, 4099, 8191, 10007,
+                               2 * 17, 34 * 9, 4 * 1009])
+def test_bluestein_sizes(n):
+    b = max(1, 2 ** 14 // n) + 1
+    x = fft_inputs.gaussian_c64(n * b, n + 7)
+    check([(n, 1, 1)], [(b, n, n)], -1, x, flags=EST, algo="ct" if n > 4096 else "auto")
+    check([(n, 1, 1)], [(b, n, n)], +1, x, flags=EST, algo="ct" if n > 4096 else "auto")
+
+
+@pytest.mark.parametrize("n", [2 ** 21, 2 ** 22, 3 * 2 ** 18, 65536 * 5])
+def test_large_multipass(n):
+    x = u(n, 77)
+    check([(n, 1, 1)], [], -1, x, flags=EST, algo="ct")
+
+
+def test_single_2_24():
+    n = 2 ** 24
+    x = u(n, fft_inputs.seed_for(1, 99))
+    check([(n, 1, 1)], [], -1, x, flags=EST, algo="ct")
+
+
+# ---------------------------------------------------------------- layouts (sec. 4.1)
+
+def test_transposed_layout_columns():
+    """dft({(n, b, 1)}, {(b, 1, n)}): columns of an n x b matrix in, rows out."""
+    for n, b in [(2187, 40), (7168, 24), (64, 100), (1000, 33)]:
+        x = fft_inputs.gaussian_c64(n * b, n)
+        check([(n, b, 1)], [(b, 1, n)], -1, x, flags=EST)
+
+
+def test_columns_in_place_example():
+    """Sec. 4.1.1 columns example, in place: dft({(n1,n2,n2)},{(n2,1,1)},X,X)."""
+    n1, n2 = 256, 96
+    x = u(n1 * n2, 5)
+    y, info = run_gpu([(n1, n2, n2)], [(n2, 1, 1)], -1, x, flags=EST, inplace=True)
+    ref = reference([(n1, n2, n2)], [(n2, 1, 1)], -1, x)
+    err = per_transform_error(y, ref, [(n1, n2, n2)], [(n2, 1, 1)])
+    assert err.max() <= TOL, info
+
+
+def test_rows_in_place_example():
+    n1, n2 = 50, 1024
+    x = u(n1 * n2, 6)
+    y, info = run_gpu([(n2, 1, 1)], [(n1, n2, n2)], +1, x, flags=EST, inplace=True)
+    ref = reference([(n2, 1, 1)], [(n1, n2, n2)], +1, x)
+    assert per_transform_error(y, ref, [(n2, 1, 1)], [(n1, n2, n2)]).max() <= TOL, info
+
+
+def test_negative_and_padded_strides():
+    n, b = 512, 9
+    x = u(2 * n * b + 8, 8)
+    # reversed input transform order and reversed elements, padded output
+    check([(n, -1, 2)], [(b, -n, 2 * n + 1)], -1, x, flags=EST, in_offset=n * b - 1)
+
+
+def test_vector_rank_two_unmergeable():
+    n = 128
+    x = u(n * 6 * 5 * 2, 9)
+    check([(n, 1, 1)], [(6, 2 * n * 5, n * 5), (5, 2 * n, n)], -1, x, flags=EST)
+
+
+def test_broadcast_zero_input_stride():
+    x = u(4, 10)
+    check([(256, 0, 1)], [(4, 1, 256)], -1, x, flags=EST)
+
+
+def test_rank0_copy_bit_exact():
+    x = u(1000, 11)
+    y, _ = run_gpu([], [(40, 25, 1), (25, 1, 40)], -1, x, flags=EST)
+    assert np.array_equal(y.reshape(25, 40), x.reshape(40, 25).T)
+
+
+def test_length_zero_is_noop():
+    x = u(16, 12)
+    y, _ = run_gpu([(0, 1, 1)], [], -1, x, out_len=16, fill=3.0, flags=EST)
+    assert np.all(y == 3.0)
+
+
+# ---------------------------------------------------------------- multi-dimensional
+
+@pytest.mark.parametrize("shape", [(12, 20), (3, 5, 7), (64, 128, 32), (256, 48), (30, 30, 30)])
+def test_multidim_small(shape):
+    dims = []
+    st = 1
+    for nn in reversed(shape):
+        dims.append((nn, st, st))
+        st *= nn
+    dims.reverse()
+    x = u(int(np.prod(shape)), 13)
+    check(dims, [], -1, x, flags=EST)
+    check(dims, [(2, st, st)], +1, np.concatenate([x, x[::-1]]), flags=EST)
+
+
+def test_rank2_4096x4096():
+    n = 4096
+    x = u(n * n, fft_inputs.seed_for(1, 50))
+    check([(n, n, n), (n, 1, 1)], [], -1, x, flags=EST, algo="ct")
+
+
+def test_rank3_256_cubed():
+    n = 256
+    x = u(n ** 3, fft_inputs.seed_for(3, 1))
+    check([(n, n * n, n * n), (n, n, n), (n, 1, 1)], [], -1, x, flags=EST, algo="ct")
+
+
+# ---------------------------------------------------------------- determinism, planner
+
+def test_repeatable_bit_exact():
+    n, b = 2048, 33
+    x = u(n * b, 14)
+    y1, _ = run_gpu([(n, 1, 1)], [(b, n, n)], -1, x, flags=EST)
+    y2, _ = run_gpu([(n, 1, 1)], [(b, n, n)], -1, x, flags=EST, repeat=3)
+    assert np.array_equal(y1, y2)
+
+
+def test_measure_and_wisdom_replay_bit_identical():
+    gbfft.fft_forget_wisdom()
+    dims, how = [(8192, 1, 1)], [(16, 8192, 8192)]
+    x = u(8192 * 16, 15)
+    y1, info1 = run_gpu(dims, how, -1, x, flags=gbfft.FFT_MEASURE)
+    wis = gbfft.fft_export_wisdom()
+    assert "r1 n=8192" in wis
+    gbfft.fft_forget_wisdom()
+    gbfft.fft_import_wisdom(wis)
+    y2, info2 = run_gpu(dims, how, -1, x, flags=gbfft.FFT_WISDOM_ONLY)
+    assert info1.replace(" estimate", "") == info2.replace(" estimate", "")
+    assert np.array_equal(y1, y2)
+    ref = reference(dims, how, -1, x, algo="ct")
+    assert per_transform_error(y2, ref, dims, how).max() <= TOL
+    gbfft.fft_forget_wisdom()
+
+
+def test_wisdom_only_without_entry_fails():
+    gbfft.fft_forget_wisdom()
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.Plan([(4096, 1, 1)], [], -1, gbfft.FFT_WISDOM_ONLY)
+    assert e.value.code == gbfft.FFT_ERR_WISDOM
+
+
+def test_alias_rejected_at_execute():
+    n = 1024
+    x = torch.zeros(2 * n, dtype=torch.complex64, device="cuda")
+    plan = gbfft.Plan([(n, 1, 1)], [], -1, EST)
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.fft_execute(plan.handle, x.data_ptr(), x.data_ptr() + 8 * (n // 2), 0)
+    assert e.value.code == gbfft.FFT_ERR_ALIAS
+    plan.destroy()
