@@ -1,0 +1,375 @@
+"""Benchmark: batched complex64 FFTs on GB300 through the library's C ABI.
+
+One step = one pass of the power-of-two sweep: for n = 2^4 .. 2^24 a batch of
+2^26 / n contiguous transforms (512 MiB in, 512 MiB out), forward and
+backward, plus a rank-2 4096 x 4096 transform and a single n = 2^24 transform,
+forward and backward.  Inputs are seeded uniform[-1, 1) complex64, resident in
+HBM and larger than L2 (no flush needed).
+
+Prints one JSON line.  ``value`` is GFLOP/s under the 5 N log2 N convention,
+summed over every transform of the step, divided by the device time of the
+step (CUDA events, max over ranks); ``e2e`` repeats the measurement through
+the same C ABI with host buffers (pinned host -> device copy of each input and
+device -> host copy of each output inside the timed region).
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+project has) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fft_inputs  # noqa: E402
+
+METRIC = "C2C FFT GFLOP/s (5n log2 n) + HBM roofline %; serve p50/p99 latency"
+WORKLOAD = ("pow2 sweep: 1D complex64 n=2^4..2^24, batch 2^26/n, contiguous, forward+backward; "
+            "plus rank-2 4096x4096 and single n=2^24, forward+backward")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("stockham.cu", "gb_pass.h", "codelets.cuh"):
+        with open(os.path.join(ROOT, "paper_2602_23525_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    valid only if the kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "stockham_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workload
+
+def workload_problems():
+    """(label, dims, howmany, n_points_per_transform, count) of one step, per sign."""
+    probs = []
+    for n in fft_inputs.POW2_SWEEP:
+        b = fft_inputs.SWEEP_POINTS // n
+        probs.append((f"n=2^{int(math.log2(n))}", [(n, 1, 1)], [(b, n, n)], n, b))
+    probs.append(("rank2 4096x4096", [(4096, 4096, 4096), (4096, 1, 1)], [], 4096 * 4096, 1))
+    probs.append(("single n=2^24", [(2 ** 24, 1, 1)], [], 2 ** 24, 1))
+    return probs
+
+
+def flops_of(n_points, count):
+    return 5.0 * n_points * math.log2(n_points) * count
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2602_23525_gb300 import gbfft
+
+    torch.cuda.set_device(args.local_rank)
+    dev = torch.device("cuda", args.local_rank)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    flags = gbfft.FFT_ESTIMATE if args.estimate else gbfft.FFT_MEASURE
+
+    x_np = fft_inputs.uniform_c64(fft_inputs.SWEEP_POINTS, fft_inputs.seed_for(1))
+    xin = torch.from_numpy(x_np).to(dev)
+    yout = torch.empty_like(xin)
+
+    t0 = time.time()
+    plans = []
+    for label, dims, how, npts, count in workload_problems():
+        for sign in (-1, 1):
+            p = gbfft.Plan(dims, how, sign, flags)
+            plans.append((label, sign, p, npts, count))
+    plan_s = time.time() - t0
+
+    def one_step(events=None):
+        for i, (label, sign, p, npts, count) in enumerate(plans):
+            if events is not None:
+                events[i][0].record(stream)
+            gbfft.fft_execute(p.handle, xin.data_ptr(), yout.data_ptr(), sptr)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in plans]
+          for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(args.local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(args.steps):
+        one_step(ev[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    step_flops = sum(flops_of(npts, count) for _, _, _, npts, count in plans)
+    step_bytes = sum(16.0 * npts * count for _, _, _, npts, count in plans)
+    ms_per_step = total_ms / args.steps
+    value = world * step_flops / (ms_per_step * 1e-3) / 1e9
+
+    # per-plan breakdown and the pass kernel's per-launch achieved bandwidth
+    per = []
+    kern_bytes = kern_ms = 0.0
+    for i, (label, sign, p, npts, count) in enumerate(plans):
+        ms = statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+        launches = p.launches
+        alg = 16.0 * npts * count
+        per.append({"problem": label, "sign": sign, "ms": round(ms, 4),
+                    "gflops": round(flops_of(npts, count) / (ms * 1e-3) / 1e9, 1),
+                    "gbs_algorithmic": round(alg / (ms * 1e-3) / 1e9, 1), "launches": launches})
+        kern_bytes += alg * launches
+        kern_ms += ms
+    peak, peak_kind = peaks()
+    achieved = kern_bytes / (kern_ms * 1e-3) / 1e9
+    traffic = recorded_traffic()
+
+    # end to end through the C ABI with host buffers (pinned), fewer steps
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(x_np).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        e2e_steps = max(1, min(args.steps, 2))
+
+        def e2e_step():
+            for label, sign, p, npts, count in plans:
+                m = npts * count
+                xin[:m].copy_(host_in[:m], non_blocking=True)
+                gbfft.fft_execute(p.handle, xin.data_ptr(), yout.data_ptr(), sptr)
+                host_out[:m].copy_(yout[:m], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / e2e_steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        nbytes = sum(8 * npts * count for _, _, _, npts, count in plans)
+        e2e = {"value": round(world * step_flops / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": round(e2e_ms, 3)}
+
+    launches = sum(p.launches for _, _, p, _, _ in plans) * args.steps
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded uniform[-1,1) complex64)",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (512 MiB per sweep point, 128 MiB "
+                   "for rank-2 and 2^24 plus 128 MiB output)", "planner": "estimate" if args.estimate else
+                   "measure", "parallelism": f"replicas x{world}",
+                   "step_bytes_algorithmic": step_bytes, "step_flops": step_flops},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4),
+                     "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
+                     "kernel": "gb_stockham_kernel (every pass of every plan)",
+                     "unit_of_work": "16 B per point per pass (each pass reads and writes every point once)",
+                     "peak_kind": f"{peak_kind} hbm_gbs",
+                     "transform_frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
+        "clocks": clk, "gpu_launches": launches, "plan_seconds": round(plan_s, 2),
+        "e2e": e2e, "per_problem": per,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    for _, _, p, _, _ in plans:
+        p.destroy()
+    return result
+
+
+# --------------------------------------------------------------------------- oracle (CPU) arm
+
+def cpu_sample(scale=1.0):
+    """Bounded sample of the sweep for the FP64 oracle: (n, transforms)."""
+    base = [(16, 4096), (256, 512), (4096, 8), (65536, 16), (2 ** 20, 1), (2 ** 24, 1)]
+    return [(n, max(1, int(c * scale))) for n, c in base]
+
+
+def time_oracle(sample):
+    import oracle
+    threads = oracle.default_threads()
+    flops = 0.0
+    t0 = time.perf_counter()
+    for n, c in sample:
+        x = fft_inputs.uniform_c64(n * c, fft_inputs.seed_for(1))
+        oracle.dft(x, [(n, 1, 1)], [(c, n, n)], -1, threads=threads)
+        flops += flops_of(n, c)
+    dt = time.perf_counter() - t0
+    return flops, dt, threads
+
+
+def cpu_baseline(budget_s=20.0):
+    flops, dt, threads = time_oracle(cpu_sample())
+    desc = ", ".join(f"{c} x n={n}" for n, c in cpu_sample())
+    return {"value": round(flops / dt / 1e9, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"forward transforms {desc} (oracle: direct eq. (1) for n<=4096, recursive "
+                      f"Cooley-Tukey above), {dt:.1f} s", "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    sample = [(16, 1024), (256, 128), (4096, 2), (65536, 4), (2 ** 20, 1)]
+    for _ in range(args.warmup):
+        time_oracle([(256, 64)])
+    tot_f = tot_t = 0.0
+    threads = 1
+    for _ in range(args.steps):
+        f, t, threads = time_oracle(sample)
+        tot_f += f
+        tot_t += t
+    value = tot_f / tot_t / 1e9
+    desc = ", ".join(f"{c} x n={n}" for n, c in sample)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * tot_t / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded uniform[-1,1) complex64)",
+            "config": {"workload": WORKLOAD, "sample_per_step": desc},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": f"per step: forward transforms {desc}"},
+            "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
+    ap.add_argument("--estimate", action="store_true", help="plan with FFT_ESTIMATE instead of measuring")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    args.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(args.local_rank)
+        torch.distributed.init_process_group("nccl")
+    res = run_gpu(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
