@@ -162,6 +162,43 @@ int fft_export_wisdom(char *buf, size_t len);
 int fft_import_wisdom(const char *text);
 void fft_forget_wisdom(void);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/* Largest batch * n that fft_execute_1d_noalloc accepts: 2^21 complex values,
+ * i.e. 16 MiB of static device scratch (plus about 129 KiB of tables and
+ * descriptors) that every GPU loading this library holds until exit. */
+#define GBFFT_NOALLOC_MAX_POINTS (1LL << 21)
+
+/*
+ * fft_execute_1d_noalloc -- a batched 1-D complex DFT that allocates no
+ * device memory, for callers that cannot allocate when they need the
+ * transform: a host thread that must not block on the device-wide
+ * synchronisation cudaMalloc/cudaFree may imply, a process whose device
+ * memory is owned by another allocator (a framework's caching allocator or a
+ * fixed pool), or a callback that is not allowed to allocate.  The paper has
+ * no counterpart; the computation is the same two-pass Cooley-Tukey step
+ * that fft_plan_dft plans for large n (n = n1 n2, both factors at most 4096
+ * with prime factors in {2,3,5,7,11,13}), using scratch, twiddle tables and
+ * pass descriptors held in one static device array.
+ *   n, batch : batch contiguous transforms of length n; element l of
+ *              transform b is at b*n + l in both in and out (complex64)
+ *   sign     : -1 forward, +1 backward (unnormalised), as fft_plan_dft
+ *   in, out  : caller-owned device arrays; in == out (in place) is allowed,
+ *              any other overlap returns FFT_ERR_ALIAS
+ *   stream   : cudaStream_t; the work is enqueued and the call returns
+ * Returns FFT_OK; FFT_ERR_UNSUPPORTED when n * batch exceeds
+ * GBFFT_NOALLOC_MAX_POINTS or n has no such split (n < 4, or a prime factor
+ * above 13); FFT_ERR_INVALID_ARG, FFT_ERR_ALIAS, FFT_ERR_CUDA.
+ * Set-up: the first call on each device looks up the static array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call rewrites the tables and the
+ * scratch it uses, so nothing carries over from the previous call, but all
+ * calls share the one array: calls that overlap on the GPU (other streams,
+ * or another host thread) race and must be serialised by the caller.
+ */
+int fft_execute_1d_noalloc(int64_t n, int64_t batch, int sign, const void *in, void *out,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

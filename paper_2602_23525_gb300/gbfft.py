@@ -72,7 +72,11 @@ _SIGNATURES = {
     "fft_export_wisdom": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t]),
     "fft_import_wisdom": (ctypes.c_int, [ctypes.c_char_p]),
     "fft_forget_wisdom": (None, []),
+    "fft_execute_1d_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
 }
+
+GBFFT_NOALLOC_MAX_POINTS = 1 << 21
 
 
 def load():
@@ -181,6 +185,15 @@ def fft_import_wisdom(text: str) -> None:
 
 def fft_forget_wisdom() -> None:
     load().fft_forget_wisdom()
+
+
+def fft_execute_1d_noalloc(n: int, batch: int, sign: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    """Batched contiguous 1-D DFT that allocates no device memory (static scratch);
+    raises GbfftError with the library's code on failure."""
+    rc = load().fft_execute_1d_noalloc(int(n), int(batch), int(sign), ctypes.c_void_p(in_ptr),
+                                       ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
+    if rc != FFT_OK:
+        raise GbfftError(rc, "fft_execute_1d_noalloc")
 
 
 # ------------------------------------------------------------------ torch helper
