@@ -165,6 +165,13 @@ struct Builder {
   // n = n1 n2 for the radix-sqrt(n) step: n1 the largest codelet-smooth divisor
   // <= sqrt(n) whose cofactor is also smooth.
   int64_t estimate_split(int64_t n) const {
+    const int lg = log2_exact(n);
+    if (lg >= 12) {
+      // powers of two: passes of at most 1024 points keep every TMA row copy
+      // of a strided pass at 64 bytes or more; three passes beyond 2^20
+      const int e1 = lg <= 20 ? lg / 2 : (lg + 2) / 3;
+      return (int64_t)1 << e1;
+    }
     int64_t best = 0;
     for (int64_t a = 2; a * a <= n; ++a)
       if (n % a == 0 && smooth_codelet(a) && smooth_codelet(n / a) &&
@@ -219,11 +226,20 @@ struct Builder {
 
   void emit_single(const Dim& d, const std::vector<Dim>& Vin, int src, int dst, int conj, const PassCfg& cfg,
                    const PostTw* tw, int depth) {
+    Step s;
+    std::string desc;
+    if (!make_single(d, Vin, src, dst, conj, cfg, tw, &s, &desc)) return;
+    P->steps.push_back(s);
+    line(depth, desc);
+  }
+
+  bool make_single(const Dim& d, const std::vector<Dim>& Vin, int src, int dst, int conj, const PassCfg& cfg,
+                   const PostTw* tw, Step* out, std::string* desc) {
     std::vector<Dim> V = Vin;
     if (V.empty()) V.push_back({1, 0, 0});
     if ((int)V.size() > GB_MAX_VDIMS || (int)cfg.radices.size() > GB_MAX_STAGES) {
       err = FFT_ERR_UNSUPPORTED;
-      return;
+      return false;
     }
     GbPass p;
     memset(&p, 0, sizeof(p));
@@ -239,7 +255,7 @@ struct Builder {
     }
     if (L != d.n) {
       err = FFT_ERR_INVALID_ARG;
-      return;
+      return false;
     }
     p.tw = roots(d.n);
     p.is = d.is;
@@ -279,15 +295,128 @@ struct Builder {
     s.smem = no_smem ? 0 : (size_t)p.T * p.pitch * sizeof(float2);
     if (s.threads > 1024 || (int64_t)s.smem > smem_limit()) {
       err = FFT_ERR_UNSUPPORTED;
-      return;
+      return false;
     }
-    P->steps.push_back(s);
     std::ostringstream o;
     o << "pass stockham n=" << d.n << " is=" << d.is << " os=" << d.os << " cfg=" << cfg.str()
       << " tpt=" << p.tpt << " threads=" << s.threads << " smem=" << s.smem << " tiles=" << p.ntiles
       << " vdims=" << dims_str(V);
     if (tw) o << " post-twiddle w_" << tw->N << "^(v0*k)";
     if (conj) o << " conj";
+    *out = s;
+    *desc = o.str();
+    return true;
+  }
+
+  static int log2_exact(int64_t n) {
+    int e = 0;
+    while ((int64_t(1) << e) < n) ++e;
+    return (int64_t(1) << e) == n ? e : -1;
+  }
+
+  // The power-of-two TMA pass kernels (stockham_pow2.cu) apply to 2^6..2^13
+  // points when one side is unit-stride along the transform (CONTIG) or along
+  // the tile dimension (ROWS / COLS), and every offset a bulk copy starts at
+  // is even (16 bytes).
+  struct P2Choice {
+    int logn = -1, load = -1, store = -1, T = 1;
+    Dim v0{1, 0, 0};
+    std::vector<Dim> rest;
+  };
+
+  static bool p2_choose(const Dim& d, const std::vector<Dim>& Vin, bool posttw, P2Choice* c) {
+    const int e = log2_exact(d.n);
+    if (e < 0 || Vin.size() > 3) return false;
+    const std::vector<Dim> V = order_for_pass(Vin);
+    P2Choice ch;
+    ch.logn = e;
+    if (!V.empty()) ch.v0 = V[0];
+    for (size_t i = 1; i < V.size(); ++i) ch.rest.push_back(V[i]);
+    const Dim& v0 = ch.v0;
+    const bool rows_ok = v0.is == 1 && (d.is % 2) == 0 && v0.n > 1;
+    const bool cols_ok = v0.os == 1 && v0.n > 1;
+    if (posttw) {
+      ch.load = rows_ok ? GB_P2_LOAD_ROWS : -1;
+      ch.store = cols_ok ? GB_P2_STORE_COLS : -1;
+    } else {
+      ch.load = d.is == 1 ? GB_P2_LOAD_CONTIG : (rows_ok ? GB_P2_LOAD_ROWS : -1);
+      ch.store = d.os == 1 ? GB_P2_STORE_CONTIG : (cols_ok ? GB_P2_STORE_COLS : -1);
+    }
+    if (ch.load < 0 || ch.store < 0 || !gb_p2_supported(e, ch.load, ch.store, posttw ? 1 : 0)) return false;
+    ch.T = gb_p2_tile(e, ch.load, ch.store);
+    if ((ch.load == GB_P2_LOAD_ROWS || ch.store == GB_P2_STORE_COLS) && v0.n % ch.T != 0) return false;
+    if (ch.load == GB_P2_LOAD_CONTIG && v0.n > 1 && (v0.is % 2) != 0) return false;
+    for (const Dim& r : ch.rest)
+      if ((r.is % 2) != 0) return false;
+    *c = ch;
+    return true;
+  }
+
+  void emit_p2(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t posttwN, int depth) {
+    P2Choice c;
+    if (!p2_choose(d, V, posttwN > 0, &c)) {
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    GbP2 k{};
+    k.logn = c.logn;
+    k.load = c.load;
+    k.store = c.store;
+    k.posttw = posttwN > 0 ? 1 : 0;
+    k.V0 = c.v0.n;
+    k.vis0 = c.v0.is;
+    k.vos0 = c.v0.os;
+    k.is = d.is;
+    k.os = d.os;
+    k.nb1 = k.nb2 = 1;
+    if (c.rest.size() > 0) {
+      k.nb1 = c.rest[0].n;
+      k.vis1 = c.rest[0].is;
+      k.vos1 = c.rest[0].os;
+    }
+    if (c.rest.size() > 1) {
+      k.nb2 = c.rest[1].n;
+      k.vis2 = c.rest[1].is;
+      k.vos2 = c.rest[1].os;
+    }
+    k.conj = conj;
+    k.status = P->d_status;
+    float2* tw = (float2*)dalloc(sizeof(float2) * (size_t)std::max(16, gb_p2_twiddle_elems(c.logn)));
+    for (int st = 1; tw && !err; ++st) {
+      int L, R, off;
+      if (!gb_p2_stage(c.logn, st, &L, &R, &off)) break;
+      if (gb_make_stage_twiddles(tw + off, d.n, L, R, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+    }
+    k.twt = tw;
+    if (k.posttw) {
+      const int64_t L = gb_p2_last_L(c.logn);
+      float2* A = (float2*)dalloc(sizeof(float2) * (size_t)(k.V0 * L));
+      float2* B = (float2*)dalloc(sizeof(float2) * (size_t)(k.V0 * 4));
+      if (A && B && gb_make_posttw(A, B, posttwN, k.V0, L, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+      k.ptwA = A;
+      k.ptwB = B;
+    }
+    // the generic pass over the same sub-problem runs when the input pointer
+    // is not 16-byte aligned
+    const std::vector<Dim> VV = order_for_pass(V);
+    Dim v0{1, 0, 0};
+    if (!VV.empty()) v0 = VV[0];
+    PostTw tw2{posttwN};
+    Step s;
+    std::string desc;
+    if (!make_single(d, VV, src, dst, conj, estimate_cfg(d, v0, !VV.empty(), default_radices(d.n)),
+                     k.posttw ? &tw2 : nullptr, &s, &desc))
+      return;
+    s.kind = STEP_POW2;
+    s.p2 = k;
+    P->steps.push_back(s);
+    static const char* ln[] = {"contig", "rows"};
+    static const char* sn[] = {"contig", "cols"};
+    std::ostringstream o;
+    o << "pass p2-tma n=" << d.n << " load=" << ln[c.load] << " store=" << sn[c.store] << " T=" << c.T
+      << " is=" << d.is << " os=" << d.os << " tile=" << dims_str({c.v0}) << " rest=" << dims_str(c.rest)
+      << (k.posttw ? " post-twiddle w_" + std::to_string(posttwN) + "^(v0*k)" : std::string()) << (conj ? " conj" : "")
+      << " (fallback: " << desc << ")";
     line(depth, o.str());
   }
 
@@ -311,9 +440,14 @@ struct Builder {
     V1.push_back({n2, d.is, 1});
     for (const Dim& v : Vs) V1.push_back(v);
     const Dim d1{n1, n2 * d.is, n2};
-    PassCfg c1 = estimate_cfg(d1, V1[0], true, default_radices(n1));
-    PostTw tw{n};
-    emit_single(d1, V1, src, S, conj, c1, &tw, depth + 1);
+    P2Choice pc;
+    if (p2_choose(d1, V1, true, &pc) && order_for_pass(V1)[0].n == n2 && order_for_pass(V1)[0].os == 1) {
+      emit_p2(d1, V1, src, S, conj, n, depth + 1);
+    } else {
+      PassCfg c1 = estimate_cfg(d1, V1[0], true, default_radices(n1));
+      PostTw tw{n};
+      emit_single(d1, V1, src, S, conj, c1, &tw, depth + 1);
+    }
     // sub-problem: n1 DFTs of size n2 over l2, output Y[k1 + k2 n1]
     std::vector<Dim> V2;
     V2.push_back({n1, n2, d.os});
@@ -463,6 +597,14 @@ struct Builder {
       v0 = V[tile_dim(V)];
       has_v = true;
     }
+    P2Choice pc;
+    if (p2_choose(d, V, false, &pc)) c.push_back("p2");
+    const int lg = log2_exact(n);
+    if (lg >= 14 && smooth_codelet(n)) {
+      // power of two beyond the one-CTA kernels: TMA passes of a split first
+      const int64_t a = estimate_split(n);
+      if (a > 1) c.push_back("split:" + std::to_string(a));
+    }
     if (smooth_codelet(n)) {
       std::vector<int> rad = default_radices(n);
       if (single_pass_ok(n, rad)) {
@@ -516,7 +658,10 @@ struct Builder {
       }
     }
     if (!smooth_codelet(n) || c.empty()) c.push_back("blue:" + std::to_string(bluestein_length(n)));
-    return c;
+    std::vector<std::string> u;
+    for (const std::string& x : c)
+      if (std::find(u.begin(), u.end(), x) == u.end()) u.push_back(x);
+    return u;
   }
 
   static int tile_dim(const std::vector<Dim>& V) {
@@ -585,7 +730,9 @@ struct Builder {
     }
     const std::string choice = choose(d, V, src == dst);
     if (err) return;
-    if (choice.rfind("single:", 0) == 0) {
+    if (choice == "p2") {
+      emit_p2(d, V, src, dst, conj, 0, depth);
+    } else if (choice.rfind("single:", 0) == 0) {
       PassCfg cfg;
       if (!cfg.parse(choice.substr(7))) {
         err = FFT_ERR_WISDOM;
@@ -663,6 +810,18 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
   switch (s.kind) {
     case STEP_PASS: {
       e = gb_launch_pass(s.pass, s.dpass, bufs[s.src], bufs[s.dst], s.threads, s.smem, s.grid, st);
+      break;
+    }
+    case STEP_POW2: {
+      if (((uintptr_t)bufs[s.src] & 15) == 0)
+      {
+        GbP2 k = s.p2;
+        k.in = bufs[s.src];
+        k.out = bufs[s.dst];
+        e = gb_launch_p2(k, st);
+      }
+      else
+        e = gb_launch_pass(s.pass, s.dpass, bufs[s.src], bufs[s.dst], s.threads, s.smem, s.grid, st);
       break;
     }
     case STEP_COPY: {

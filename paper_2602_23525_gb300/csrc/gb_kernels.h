@@ -12,6 +12,32 @@ cudaError_t gb_launch_pass(const GbPass& p, const GbPass* dev, const float2* in,
 cudaError_t gb_launch_copy(const GbCopy& c, cudaStream_t st);
 int gb_pass_max_smem_optin(void);
 
+// Power-of-two pass kernels with TMA tile loads (stockham_pow2.cu),
+// n = 2^6 .. 2^13.  Transforms of length n along (is, os); the tile dimension
+// (V0, vis0, vos0) holds T adjacent transforms per CTA; up to two more
+// vector loops (nb1, vis1, vos1), (nb2, vis2, vos2).
+enum { GB_P2_LOAD_CONTIG = 0, GB_P2_LOAD_ROWS = 1 };     // is == 1  |  vis0 == 1
+enum { GB_P2_STORE_CONTIG = 0, GB_P2_STORE_COLS = 1 };   // os == 1  |  vos0 == 1
+struct GbP2 {
+  int logn, load, store, posttw;
+  const float2* in;   // set at execute time
+  float2* out;
+  int64_t V0, is, os, vis0, vos0;
+  int64_t nb1, nb2, vis1, vos1, vis2, vos2;
+  int conj;
+  const float2* twt;   // per-stage [k][4] twiddle tables (gb_make_stage_twiddles)
+  const float2* ptwA;  // post twiddle: A[c*L + j] = w_N^{c j}
+  const float2* ptwB;  //               B[c] = (s, s^2, s^4, s^8), s = w_N^{c L}
+  int* status;
+  int64_t grid;        // <= 0: persistent grid sized by occupancy
+};
+int gb_p2_supported(int logn, int load, int store, int posttw);
+int gb_p2_tile(int logn, int load, int store);   // transforms per CTA tile
+int gb_p2_twiddle_elems(int logn);               // float2 entries of the stage tables
+int gb_p2_stage(int logn, int s, int* L, int* R, int* offset);
+int gb_p2_last_L(int logn);
+cudaError_t gb_launch_p2(const GbP2& k, cudaStream_t st);
+
 // Bluestein helper kernels for convolution lengths beyond one CTA (bluestein.cu).
 struct GbBlueIO {
   const float2* in;     // user input, element 0
@@ -33,5 +59,10 @@ cudaError_t gb_launch_blue_post(const GbBlueIO& b, const float2* data, cudaStrea
 // FP64 table generation (tables.cu).
 cudaError_t gb_make_roots(float2* out, int64_t count, int64_t N, int64_t mult, cudaStream_t st);
 cudaError_t gb_make_chirp(float2* out, int64_t n, cudaStream_t st);
+// out[k*4 + i] = w_N^{p k N/(L R)} for k < L and p = 1, 2, 4, 8 (i = log2 p)
+cudaError_t gb_make_stage_twiddles(float2* out, int64_t N, int64_t L, int R, cudaStream_t st);
+// four-step post twiddles w_N^{c k}, k = j + q L: A[c*L + j] = w_N^{c j},
+// B[c*4 + i] = w_N^{c L 2^i}, for c < ncols, j < L
+cudaError_t gb_make_posttw(float2* A, float2* B, int64_t N, int64_t ncols, int64_t L, cudaStream_t st);
 cudaError_t gb_make_bluestein_kernel(float2* out, int64_t n, int64_t m, const int* radices, int nrad,
                                      double2* work, cudaStream_t st);

@@ -35,7 +35,7 @@ struct PassCfg {
   bool parse(const std::string& s);
 };
 
-enum StepKind { STEP_PASS = 0, STEP_COPY = 1, STEP_BLUE_PRE = 2, STEP_BLUE_MUL = 3, STEP_BLUE_POST = 4 };
+enum StepKind { STEP_PASS = 0, STEP_COPY = 1, STEP_BLUE_PRE = 2, STEP_BLUE_MUL = 3, STEP_BLUE_POST = 4, STEP_POW2 = 5 };
 
 // Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.
 enum { BUF_IN = 0, BUF_OUT = 1, BUF_SCRATCH0 = 2 };
@@ -44,6 +44,8 @@ struct Step {
   int kind = STEP_PASS;
   GbPass pass{};
   const GbPass* dpass = nullptr;  // device copy of pass (what the kernel reads)
+  GbP2 p2{};                      // STEP_POW2; pass/dpass hold the generic fallback
+                                  // used when the input pointer is not 16-byte aligned
   GbCopy copy{};
   GbBlueIO blue{};
   int src = BUF_IN, dst = BUF_OUT;

@@ -1,0 +1,452 @@
+// stockham_pow2.cu -- batched power-of-two Stockham pass kernels with TMA tile
+// loads (sm_103a), n = 2^6 .. 2^13.
+//
+// The Stockham stages of stockham.cu (eq. (2) applied with n1 = L, n2 = R at
+// every stage, output auto-sorted, sec. 2), specialised at compile time: the
+// radix schedule is 2^(log2 n mod 4) first (when not 1) and 16 after, every
+// thread holds exactly 16 values (n/16 threads per transform), index
+// arithmetic is shifts and masks, and the stage twiddles w_{16L}^{r k} come
+// from per-stage tables [k][4] = (w, w^2, w^4, w^8) (two 128-bit loads; every
+// other power is a product of at most three entries -- the small-table
+// scheme of sec. 6, never a running recurrence).
+//
+// A CTA computes a tile of T transforms that are adjacent along the tile
+// dimension of the vector loops, and is persistent over tiles.  One warp
+// issues TMA bulk copies (cp.async.bulk, completion counted on an mbarrier)
+// of the next NBUF tiles while all threads compute the current one, so HBM
+// reads stay in flight through the compute phases (the buffered copies of
+// sec. 3.3, done by the copy engine).  Two tile shapes:
+//   LOAD_CONTIG: each transform is contiguous (unit element stride); one copy
+//                per tile when the tile's transforms are adjacent, else one per
+//                transform.
+//   LOAD_ROWS:   the tile is T adjacent columns of a row-major matrix whose
+//                columns are the transforms (unit stride along the tile
+//                dimension): one copy of T elements per row -- the strided
+//                first pass of a four-step plan (sec. 3.3, radix-sqrt(n)).
+// and two store shapes: STORE_CONTIG (unit element stride, lanes along the
+// transform) and STORE_COLS (unit stride along the tile dimension, lanes
+// across the T transforms, so T adjacent outputs form one segment).
+// With POSTTW the outputs are multiplied by the four-step twiddle
+// w_N^{l2 k1} of eq. (2) (l2 = column, k1 = output index).
+// Every mbarrier wait is bounded by %globaltimer; on timeout the CTA records
+// FFT_ERR_DEVICE_TIMEOUT in the status word and returns.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "codelets.cuh"
+#include "gb_kernels.h"
+
+namespace {
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr int kStatusTimeout = 8;                              // FFT_ERR_DEVICE_TIMEOUT
+
+template <int LOGN>
+struct P2 {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int REM = LOGN % 4;
+  static constexpr int R0 = REM ? (1 << REM) : 16;
+  static constexpr int NST = LOGN / 4 + (REM ? 1 : 0);
+  static constexpr int TPT = N / 16;
+  static constexpr int PITCH = ((N + (N - 1) / 32 + 1) | 1);
+  __host__ __device__ static constexpr int radix(int s) { return s == 0 ? R0 : 16; }
+  __host__ __device__ static constexpr int L(int s) { return s == 0 ? 1 : R0 << (4 * (s - 1)); }
+  // stage s >= 1 table: [k][4] = (w, w^2, w^4, w^8), w = w_{16 L}^k
+  __host__ __device__ static constexpr int twoff(int s) {
+    int o = 0;
+    for (int i = 1; i < s; ++i) o += L(i) * 4;
+    return o;
+  }
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ int phys(int i) { return i + (i >> 5); }
+
+template <int R>
+__device__ __forceinline__ void codelet(float2* v);
+template <> __device__ __forceinline__ void codelet<2>(float2* v) { gb_dft2(v); }
+template <> __device__ __forceinline__ void codelet<4>(float2* v) { gb_dft4(v); }
+template <> __device__ __forceinline__ void codelet<8>(float2* v) { gb_dft8(v); }
+template <> __device__ __forceinline__ void codelet<16>(float2* v) { gb_dft16(v); }
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for phase `parity` of the mbarrier at `bar`
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try(bar, parity))
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// the powers w^1..w^15 from (w, w^2, w^4, w^8), at most three products each
+__device__ __forceinline__ void powers16(float2* p, const float4* tw) {
+  const float4 a = __ldg(tw), b = __ldg(tw + 1);
+  p[1] = make_float2(a.x, a.y);
+  p[2] = make_float2(a.z, a.w);
+  p[4] = make_float2(b.x, b.y);
+  p[8] = make_float2(b.z, b.w);
+  p[3] = cmul(p[2], p[1]);
+  p[5] = cmul(p[4], p[1]);
+  p[6] = cmul(p[4], p[2]);
+  p[7] = cmul(p[4], p[3]);
+#pragma unroll
+  for (int r = 9; r < 16; ++r) p[r] = cmul(p[8], p[r - 8]);
+}
+
+__device__ __forceinline__ void twiddle16(float2* v, const float4* tw) {
+  float2 p[16];
+  powers16(p, tw);
+#pragma unroll
+  for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], p[r]);
+}
+
+// Stage S reads (+ twiddles + butterfly) for butterflies j = u + b*TPT of one
+// transform: from its padded exchange row, or (stage 0) from the landed tile
+// where element e sits at src[e * ESTRIDE].
+template <int LOGN, int S, bool FROM_TILE, int ESTRIDE>
+__device__ __forceinline__ void stage_in(float2* v, const float2* src, const float2* __restrict__ twt, int u,
+                                         int conj) {
+  using C = P2<LOGN>;
+  constexpr int R = C::radix(S), B = 16 / R, NB = C::N / R, L = C::L(S);
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = u + b * C::TPT;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int idx = j + r * NB;
+      float2 x = FROM_TILE ? src[idx * ESTRIDE] : src[phys(idx)];
+      if (FROM_TILE && conj) x.y = -x.y;
+      v[b * R + r] = x;
+    }
+    if constexpr (L > 1) {
+      static_assert(R == 16, "twiddled stages are radix 16");
+      const int k = j & (L - 1);
+      twiddle16(v + b * R, reinterpret_cast<const float4*>(twt + C::twoff(S) + k * 4));
+    }
+    codelet<R>(v + b * R);
+  }
+}
+
+// Stage S writes to the padded exchange row
+template <int LOGN, int S>
+__device__ __forceinline__ void stage_out_x(const float2* v, float2* dst, int u) {
+  using C = P2<LOGN>;
+  constexpr int R = C::radix(S), B = 16 / R, L = C::L(S);
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = u + b * C::TPT;
+    const int k = j & (L - 1);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dst[phys(base + q * L)] = v[b * R + q];
+  }
+}
+
+// Last stage writes global memory: output k = j + q*L of the transform goes
+// to dst[k * ostride].  POSTTW multiplies output k of column l2 by
+// w_N^{l2 k} = A[l2 L + j] * s^q with s = w_N^{l2 L} from B[l2] = (s, s^2, s^4, s^8).
+template <int LOGN, bool POSTTW>
+__device__ __forceinline__ void stage_out_g(const float2* v, float2* dst, int64_t ostride, int u, int conj,
+                                            const float2* __restrict__ A, const float2* __restrict__ Bt,
+                                            int64_t col) {
+  using C = P2<LOGN>;
+  constexpr int S = C::NST - 1;
+  constexpr int R = C::radix(S), B = 16 / R, L = C::L(S);
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = u + b * C::TPT;  // j < L in the last stage
+    float2 p[16];
+    float2 a = make_float2(1.f, 0.f);
+    if constexpr (POSTTW) {
+      static_assert(R == 16, "post twiddles need a radix-16 last stage");
+      powers16(p, reinterpret_cast<const float4*>(Bt + col * 4));
+      a = __ldg(A + col * L + j);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      float2 x = v[b * R + q];
+      if constexpr (POSTTW) x = cmul(x, q == 0 ? a : cmul(a, p[q]));
+      if (conj) x.y = -x.y;
+      dst[(int64_t)(j + q * L) * ostride] = x;
+    }
+  }
+}
+
+template <int LOGN, int S, bool POSTTW>
+__device__ __forceinline__ void later_stages(float2* v, float2* xrow_j, float2* xrow_s, float2* gout,
+                                             int64_t ostride, const float2* __restrict__ twt, int uj, int us,
+                                             int conj, bool valid, const float2* A, const float2* Bt, int64_t col) {
+  using C = P2<LOGN>;
+  if constexpr (S < C::NST) {
+    if constexpr (S == C::NST - 1) {
+      // the last stage runs in the store mapping
+      stage_in<LOGN, S, false, 1>(v, xrow_s, twt, us, conj);
+      if (valid) stage_out_g<LOGN, POSTTW>(v, gout, ostride, us, conj, A, Bt, col);
+    } else {
+      stage_in<LOGN, S, false, 1>(v, xrow_j, twt, uj, conj);
+      __syncthreads();
+      stage_out_x<LOGN, S>(v, xrow_j, uj);
+      __syncthreads();
+      later_stages<LOGN, S + 1, POSTTW>(v, xrow_j, xrow_s, gout, ostride, twt, uj, us, conj, valid, A, Bt, col);
+    }
+  }
+}
+
+// Thread -> (transform t, thread u within the transform):
+//   "j-fast": t = tid / TPT, u = tid % TPT (lanes along a transform)
+//   "t-fast": t = tid % T,   u = tid / T   (lanes across the T transforms)
+// Stage 0 uses the mapping that reads the landed tile without bank conflicts,
+// the last stage the one that makes the global stores coalesce.
+template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW>
+__global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB) gb_p2_kernel(const __grid_constant__ GbP2 k) {
+  using C = P2<LOGN>;
+  constexpr int TILE = T * C::N;  // elements per tile buffer
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  float2* ibuf = reinterpret_cast<float2*>(smem_raw + 128);
+  float2* xbuf = ibuf + NBUF * TILE;
+
+  const int tid = threadIdx.x;
+  const int tj = tid / C::TPT, uj = tid - tj * C::TPT;  // j-fast
+  const int tt = tid % T, ut = tid / T;                 // t-fast
+  const int t0 = (LOAD == GB_P2_LOAD_ROWS) ? tt : tj;
+  const int u0 = (LOAD == GB_P2_LOAD_ROWS) ? ut : uj;
+  const int ts = (STORE == GB_P2_STORE_COLS) ? tt : tj;
+  const int us = (STORE == GB_P2_STORE_COLS) ? ut : uj;
+
+  const int64_t cblocks = (k.V0 + T - 1) / T;
+  const int64_t ntiles = cblocks * k.nb1 * k.nb2;
+
+  if (tid == 0) {
+    for (int b = 0; b < NBUF; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // tile -> element offsets of its transform 0 and its first index along the tile dim
+  auto origin = [&](int64_t tile, int64_t* ib, int64_t* ob, int64_t* c0) {
+    const int64_t cb = tile % cblocks;
+    const int64_t r = tile / cblocks;
+    const int64_t b1 = r % k.nb1, b2 = r / k.nb1;
+    *c0 = cb * T;
+    *ib = b1 * k.vis1 + b2 * k.vis2 + *c0 * k.vis0;
+    *ob = b1 * k.vos1 + b2 * k.vos2 + *c0 * k.vos0;
+  };
+
+  // warp 0 issues the copies of one tile into buffer b
+  auto issue = [&](int b, int64_t tile) {
+    int64_t ib, ob, c0;
+    origin(tile, &ib, &ob, &c0);
+    const int64_t cnt = (k.V0 - c0) < T ? (k.V0 - c0) : T;
+    const uint32_t bar = smem_addr(bars + b);
+    float2* dst = ibuf + b * TILE;
+    const int lane = tid & 31;
+    if (LOAD == GB_P2_LOAD_CONTIG) {
+      if (lane == 0) expect_tx(bar, (uint32_t)(cnt * C::N * 8));
+      __syncwarp();
+      if (T == 1 || k.vis0 == C::N) {
+        if (lane == 0) bulk_copy(smem_addr(dst), k.in + ib, (uint32_t)(cnt * C::N * 8), bar);
+      } else {
+        for (int64_t i = lane; i < cnt; i += 32)
+          bulk_copy(smem_addr(dst + i * C::N), k.in + ib + i * k.vis0, (uint32_t)(C::N * 8), bar);
+      }
+    } else {
+      // rows of T adjacent columns (the host makes V0 a multiple of T):
+      // element e of column t lands at dst[e * T + t]
+      if (lane == 0) expect_tx(bar, (uint32_t)(C::N * T * 8));
+      __syncwarp();
+      for (int e = lane; e < C::N; e += 32)
+        bulk_copy(smem_addr(dst + e * T), k.in + ib + (int64_t)e * k.is, (uint32_t)(T * 8), bar);
+    }
+  };
+
+  if (tid < 32) {
+    for (int b = 0; b < NBUF; ++b) {
+      const int64_t tile = blockIdx.x + (int64_t)b * gridDim.x;
+      if (tile < ntiles) issue(b, tile);
+    }
+  }
+
+  float2 v[16];
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it % NBUF;
+    const uint32_t parity = (uint32_t)((it / NBUF) & 1);
+    const bool ok = mbar_wait(smem_addr(bars + b), parity);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
+      return;
+    }
+    int64_t ib, ob, c0;
+    origin(tile, &ib, &ob, &c0);
+    const int64_t cnt = (k.V0 - c0) < T ? (k.V0 - c0) : T;
+    const bool valid = ts < cnt;
+    float2* gout = k.out + ob + (int64_t)ts * k.vos0;
+    const int64_t ostride = (STORE == GB_P2_STORE_COLS) ? k.os : 1;
+    const int64_t col = c0 + ts;  // post-twiddle column index (tile dimension)
+    const float2* tile_buf = ibuf + b * TILE;
+    if constexpr (LOAD == GB_P2_LOAD_ROWS)
+      stage_in<LOGN, 0, true, T>(v, tile_buf + t0, k.twt, u0, k.conj);
+    else
+      stage_in<LOGN, 0, true, 1>(v, tile_buf + t0 * C::N, k.twt, u0, k.conj);
+    __syncthreads();  // tile buffer b fully read; previous tile's exchange reads done
+    if (tid < 32) {
+      const int64_t next = tile + (int64_t)NBUF * gridDim.x;
+      if (next < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(b, next);
+      }
+    }
+    if constexpr (C::NST == 1) {
+      // one stage: the host only builds this when both mappings agree
+      if (valid) stage_out_g<LOGN, POSTTW>(v, gout, ostride, u0, k.conj, k.ptwA, k.ptwB, col);
+    } else {
+      stage_out_x<LOGN, 0>(v, xbuf + t0 * C::PITCH, u0);
+      __syncthreads();
+      later_stages<LOGN, 1, POSTTW>(v, xbuf + tj * C::PITCH, xbuf + ts * C::PITCH, gout, ostride, k.twt, uj, us,
+                                    k.conj, valid, k.ptwA, k.ptwB, col);
+    }
+  }
+}
+
+template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW>
+cudaError_t launch(const GbP2& k, cudaStream_t st) {
+  using C = P2<LOGN>;
+  const size_t smem = 128 + sizeof(float2) * ((size_t)NBUF * T * C::N + (C::NST > 1 ? (size_t)T * C::PITCH : 0));
+  auto fn = gb_p2_kernel<LOGN, T, NBUF, MINB, LOAD, STORE, POSTTW>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T * C::TPT, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = ((k.V0 + T - 1) / T) * k.nb1 * k.nb2;
+  int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  if (k.grid > 0) grid = k.grid;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) return cudaSuccess;
+  fn<<<(unsigned)grid, T * C::TPT, smem, st>>>(k);
+  return cudaGetLastError();
+}
+
+// transforms per CTA tile, by size and tile shape (tiles of 32-64 KB)
+constexpr int tile_T(int logn, int load, int store) {
+  return (load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG)
+             ? (logn <= 12 ? (1 << (12 - logn)) : 1)
+             : (logn <= 9 ? 16 : (logn == 10 ? 8 : (logn == 11 ? 4 : 2)));
+}
+
+constexpr int min_blocks(int logn, int load, int store) {
+  return (load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG) ? (logn <= 12 ? 2 : 1) : (logn <= 8 ? 2 : 1);
+}
+
+template <int LOGN, int LOAD, int STORE, bool POSTTW>
+cudaError_t launch_n(const GbP2& k, cudaStream_t st) {
+  return launch<LOGN, tile_T(LOGN, LOAD, STORE), 2, min_blocks(LOGN, LOAD, STORE), LOAD, STORE, POSTTW>(k, st);
+}
+
+template <int LOAD, int STORE, bool POSTTW>
+cudaError_t dispatch(const GbP2& k, cudaStream_t st) {
+  constexpr bool cc = LOAD == GB_P2_LOAD_CONTIG && STORE == GB_P2_STORE_CONTIG;
+  switch (k.logn) {
+    case 6: if constexpr (!cc) return launch_n<6, LOAD, STORE, POSTTW>(k, st); break;
+    case 7: if constexpr (!cc) return launch_n<7, LOAD, STORE, POSTTW>(k, st); break;
+    case 8: return launch_n<8, LOAD, STORE, POSTTW>(k, st);
+    case 9: return launch_n<9, LOAD, STORE, POSTTW>(k, st);
+    case 10: return launch_n<10, LOAD, STORE, POSTTW>(k, st);
+    case 11: return launch_n<11, LOAD, STORE, POSTTW>(k, st);
+    case 12: return launch_n<12, LOAD, STORE, POSTTW>(k, st);
+    case 13: if constexpr (cc && !POSTTW) return launch_n<13, LOAD, STORE, POSTTW>(k, st); break;
+    default: break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int gb_p2_supported(int logn, int load, int store, int posttw) {
+  const bool cc = load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG;
+  if (cc) return !posttw && logn >= 8 && logn <= 13;
+  if (logn < 6 || logn > 12) return 0;
+  if (posttw && !(load == GB_P2_LOAD_ROWS && store == GB_P2_STORE_COLS)) return 0;
+  if (posttw && logn % 4 != 0 && logn / 4 + 1 < 2) return 0;
+  return 1;
+}
+
+int gb_p2_tile(int logn, int load, int store) { return tile_T(logn, load, store); }
+
+int gb_p2_twiddle_elems(int logn) {
+  const int rem = logn % 4, r0 = rem ? (1 << rem) : 16, nst = logn / 4 + (rem ? 1 : 0);
+  int o = 0;
+  for (int i = 1; i < nst; ++i) o += (r0 << (4 * (i - 1))) * 4;
+  return o;
+}
+
+// stage s >= 1 of the schedule: (L, R) and the table offset, for the generator
+int gb_p2_stage(int logn, int s, int* L, int* R, int* offset) {
+  const int rem = logn % 4, r0 = rem ? (1 << rem) : 16, nst = logn / 4 + (rem ? 1 : 0);
+  if (s < 1 || s >= nst) return 0;
+  *R = 16;
+  *L = r0 << (4 * (s - 1));
+  int o = 0;
+  for (int i = 1; i < s; ++i) o += (r0 << (4 * (i - 1))) * 4;
+  *offset = o;
+  return 1;
+}
+
+// L of the last stage (the post-twiddle table has N_cols x L base entries)
+int gb_p2_last_L(int logn) {
+  const int rem = logn % 4, r0 = rem ? (1 << rem) : 16, nst = logn / 4 + (rem ? 1 : 0);
+  return nst <= 1 ? 1 : (r0 << (4 * (nst - 2)));
+}
+
+cudaError_t gb_launch_p2(const GbP2& k, cudaStream_t st) {
+  if (k.load == GB_P2_LOAD_CONTIG && k.store == GB_P2_STORE_CONTIG)
+    return dispatch<GB_P2_LOAD_CONTIG, GB_P2_STORE_CONTIG, false>(k, st);
+  if (k.load == GB_P2_LOAD_CONTIG && k.store == GB_P2_STORE_COLS)
+    return dispatch<GB_P2_LOAD_CONTIG, GB_P2_STORE_COLS, false>(k, st);
+  if (k.load == GB_P2_LOAD_ROWS && k.store == GB_P2_STORE_CONTIG)
+    return dispatch<GB_P2_LOAD_ROWS, GB_P2_STORE_CONTIG, false>(k, st);
+  if (k.load == GB_P2_LOAD_ROWS && k.store == GB_P2_STORE_COLS)
+    return k.posttw ? dispatch<GB_P2_LOAD_ROWS, GB_P2_STORE_COLS, true>(k, st)
+                    : dispatch<GB_P2_LOAD_ROWS, GB_P2_STORE_COLS, false>(k, st);
+  return cudaErrorInvalidValue;
+}

@@ -23,6 +23,46 @@ __global__ void gb_roots_kernel(float2* out, int64_t count, int64_t N, int64_t m
   }
 }
 
+// per-stage table [k][4]: w_N^{(p k step) mod N} for p = 1, 2, 4, 8, step = N/(L R)
+__global__ void gb_stage_tw_kernel(float2* out, int64_t N, int64_t L, int R) {
+  const int64_t total = L * 4;
+  const int64_t step = N / (L * R);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t k = i >> 2;
+    const int64_t r = (int64_t)1 << (i & 3);
+    float2 w = make_float2(1.f, 0.f);
+    if (r < R) {
+      const int64_t m = (int64_t)(((unsigned long long)(r * k) * (unsigned long long)step) % (unsigned long long)N);
+      double s, c;
+      sincospi(2.0 * (double)m / (double)N, &s, &c);
+      w = make_float2((float)c, (float)(-s));
+    }
+    out[i] = w;
+  }
+}
+
+__device__ __forceinline__ float2 root64(int64_t m, int64_t N) {
+  double s, c;
+  sincospi(2.0 * (double)m / (double)N, &s, &c);
+  return make_float2((float)c, (float)(-s));
+}
+
+__global__ void gb_posttw_kernel(float2* A, float2* B, int64_t N, int64_t ncols, int64_t L) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t na = ncols * L;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + ncols * 4; i += stride) {
+    if (i < na) {
+      const int64_t c = i / L, j = i - (i / L) * L;
+      A[i] = root64((int64_t)(((unsigned long long)c * (unsigned long long)j) % (unsigned long long)N), N);
+    } else {
+      const int64_t q = i - na, c = q >> 2, p = (int64_t)1 << (q & 3);
+      const unsigned long long e = ((unsigned long long)c * (unsigned long long)(L * p)) % (unsigned long long)N;
+      B[q] = root64((int64_t)e, N);
+    }
+  }
+}
+
 // chirp w_k = exp(-pi i (k^2 mod 2n) / n), k < n   (Bluestein)
 __global__ void gb_chirp_kernel(float2* out, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -96,6 +136,17 @@ unsigned grid_for(int64_t count) {
 cudaError_t gb_make_roots(float2* out, int64_t count, int64_t N, int64_t mult, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   gb_roots_kernel<<<grid_for(count), 256, 0, st>>>(out, count, N, mult);
+  return cudaGetLastError();
+}
+
+cudaError_t gb_make_stage_twiddles(float2* out, int64_t N, int64_t L, int R, cudaStream_t st) {
+  if (L <= 0) return cudaSuccess;
+  gb_stage_tw_kernel<<<grid_for(L * 4), 256, 0, st>>>(out, N, L, R);
+  return cudaGetLastError();
+}
+
+cudaError_t gb_make_posttw(float2* A, float2* B, int64_t N, int64_t ncols, int64_t L, cudaStream_t st) {
+  gb_posttw_kernel<<<grid_for(ncols * (L + 4)), 256, 0, st>>>(A, B, N, ncols, L);
   return cudaGetLastError();
 }
 

@@ -122,10 +122,15 @@ def test_plan_mixed_radix():
 
 
 def test_plan_large_is_multi_pass():
+    """Radix-sqrt(n) steps (sec. 3.3): 2^24 = 256 x 65536, the 65536-point rows
+    again split 256 x 256 -- three passes, each a one-CTA TMA pass kernel."""
     t = explain([(2 ** 24, 1, 1)])
-    assert "cooley-tukey n=16777216 = 4096 x 4096" in t
-    assert t.count("pass stockham") == 2
-    assert "post-twiddle" in t
+    assert "cooley-tukey n=16777216 = 256 x 65536" in t
+    assert "cooley-tukey n=65536 = 256 x 256" in t
+    assert t.count("pass p2-tma") == 3
+    assert t.count("post-twiddle") >= 2
+    t = explain([(2 ** 20, 1, 1)], [(4, 2 ** 20, 2 ** 20)])
+    assert "= 1024 x 1024" in t and t.count("pass p2-tma") == 2
 
 
 def test_plan_prime_is_bluestein():

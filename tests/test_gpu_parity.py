@@ -203,3 +203,57 @@ def test_alias_rejected_at_execute():
         gbfft.fft_execute(plan.handle, x.data_ptr(), x.data_ptr() + 8 * (n // 2), 0)
     assert e.value.code == gbfft.FFT_ERR_ALIAS
     plan.destroy()
+
+
+# ---------------------------------------------------------------- power-of-two TMA kernel
+
+@pytest.mark.parametrize("e", range(8, 14))
+def test_pow2_kernel_padded_batch_stride(e):
+    """Batch stride n + 2 (tiles are not one contiguous block: one bulk copy per
+    transform) and a ragged last tile."""
+    n = 2 ** e
+    b = 37
+    x = u((n + 2) * b, 30 + e)
+    err, info = check([(n, 1, 1)], [(b, n + 2, n)], -1, x, flags=EST)
+    assert "p2-tma" in info
+
+
+def test_pow2_kernel_unaligned_input_falls_back():
+    """An input pointer that is 8- but not 16-byte aligned cannot feed a bulk copy;
+    the plan's generic pass runs instead, with the same result."""
+    n, b = 1024, 9
+    x = u(n * b + 1, 31)
+    err, info = check([(n, 1, 1)], [(b, n, n)], +1, x, flags=EST, in_offset=1)
+    assert "p2-tma" in info
+
+
+def test_pow2_kernel_matches_generic_pass_bit_for_bit_tolerance():
+    """The specialised kernel and the generic pass run the same stage schedule;
+    both stay within the oracle tolerance for every size (forward, in place)."""
+    for e in range(8, 14):
+        n = 2 ** e
+        b = 2 ** 20 // n
+        x = u(n * b, 40 + e)
+        y, info = run_gpu([(n, 1, 1)], [(b, n, n)], -1, x, flags=EST, inplace=True)
+        assert "p2-tma" in info
+        ref = reference([(n, 1, 1)], [(b, n, n)], -1, x, algo="ct")
+        assert per_transform_error(y, ref, [(n, 1, 1)], [(b, n, n)]).max() <= TOL
+
+
+def test_p2_strided_tile_shapes():
+    """Column tiles (rows of adjacent columns in, rows or columns out) of the TMA
+    pass kernels, with two extra vector loops and ragged column counts rejected
+    back to the generic pass."""
+    for n, cols, b in [(64, 48, 3), (512, 32, 2), (1024, 16, 2), (4096, 4, 2)]:
+        x = u(n * cols * b, 50 + n)
+        # columns of a row-major n x cols matrix, b matrices
+        err, info = check([(n, cols, cols)], [(cols, 1, 1), (b, n * cols, n * cols)], +1, x, flags=EST)
+        assert "p2-tma" in info and "load=rows" in info
+        err, info = check([(n, cols, 1)], [(cols, 1, n), (b, n * cols, n * cols)], -1, x, flags=EST)
+        assert "load=rows store=contig" in info
+    x = u(1024 * 24, 60)
+    err, info = check([(1024, 1, 24)], [(24, 1024, 1)], -1, x, flags=EST)
+    assert "load=contig store=cols" in info
+    x = u(1024 * 20, 61)
+    err, info = check([(1024, 1, 20)], [(20, 1024, 1)], -1, x, flags=EST)
+    assert "p2-tma" not in info and "pass stockham" in info
