@@ -344,6 +344,11 @@ struct Builder {
     }
     if (ch.load < 0 || ch.store < 0 || !gb_p2_supported(e, ch.load, ch.store, posttw ? 1 : 0)) return false;
     ch.T = gb_p2_tile(e, ch.load, ch.store);
+    if (ch.load == GB_P2_LOAD_CONTIG && ch.store == GB_P2_STORE_CONTIG && gb_p2_small(e)) {
+      // small transforms: adjacent on both sides, one vector loop
+      if (!ch.rest.empty() || (v0.n > 1 && (v0.is != d.n || v0.os != d.n))) return false;
+      ch.T = 4096 >> e;
+    }
     if ((ch.load == GB_P2_LOAD_ROWS || ch.store == GB_P2_STORE_COLS) && v0.n % ch.T != 0) return false;
     if (ch.load == GB_P2_LOAD_CONTIG && v0.n > 1 && (v0.is % 2) != 0) return false;
     for (const Dim& r : ch.rest)
@@ -813,7 +818,8 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
       break;
     }
     case STEP_POW2: {
-      if (((uintptr_t)bufs[s.src] & 15) == 0)
+      const bool small = s.p2.load == GB_P2_LOAD_CONTIG && s.p2.store == GB_P2_STORE_CONTIG && gb_p2_small(s.p2.logn);
+      if (((uintptr_t)bufs[s.src] & 15) == 0 && (!small || ((uintptr_t)bufs[s.dst] & 15) == 0))
       {
         GbP2 k = s.p2;
         k.in = bufs[s.src];

@@ -13,7 +13,7 @@ cudaError_t gb_launch_copy(const GbCopy& c, cudaStream_t st);
 int gb_pass_max_smem_optin(void);
 
 // Power-of-two pass kernels with TMA tile loads (stockham_pow2.cu),
-// n = 2^6 .. 2^13.  Transforms of length n along (is, os); the tile dimension
+// n = 2^4 .. 2^13.  Transforms of length n along (is, os); the tile dimension
 // (V0, vis0, vos0) holds T adjacent transforms per CTA; up to two more
 // vector loops (nb1, vis1, vos1), (nb2, vis2, vos2).
 enum { GB_P2_LOAD_CONTIG = 0, GB_P2_LOAD_ROWS = 1 };     // is == 1  |  vis0 == 1
@@ -33,6 +33,7 @@ struct GbP2 {
 };
 int gb_p2_supported(int logn, int load, int store, int posttw);
 int gb_p2_tile(int logn, int load, int store);   // transforms per CTA tile
+int gb_p2_small(int logn);                       // 1: n = 2^logn uses the small-transform kernel
 int gb_p2_twiddle_elems(int logn);               // float2 entries of the stage tables
 int gb_p2_stage(int logn, int s, int* L, int* R, int* offset);
 int gb_p2_last_L(int logn);

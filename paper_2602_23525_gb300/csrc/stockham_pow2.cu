@@ -1,5 +1,5 @@
 // stockham_pow2.cu -- batched power-of-two Stockham pass kernels with TMA tile
-// loads (sm_103a), n = 2^6 .. 2^13.
+// loads (sm_103a), n = 2^4 .. 2^13.
 //
 // The Stockham stages of stockham.cu (eq. (2) applied with n1 = L, n2 = R at
 // every stage, output auto-sorted, sec. 2), specialised at compile time: the
@@ -367,6 +367,120 @@ cudaError_t launch(const GbP2& k, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Small transforms, n = 16 .. 128, contiguous tiles of 4096 points (T = 4096/n
+// transforms) in and out.  Landing a tile of many short transforms unpadded
+// would make every stage-0 read a bank conflict (the transforms sit a multiple
+// of 32 banks apart), so after the bulk copy lands the CTA re-lays it into
+// odd-pitch rows with 128-bit reads; every stage then runs with lanes across
+// the transforms, and the outputs leave from the rows with 128-bit stores.
+template <int LOGN>
+__global__ void __launch_bounds__(256, 2) gb_p2small_kernel(const __grid_constant__ GbP2 k) {
+  using C = P2<LOGN>;
+  constexpr int T = 4096 / C::N;
+  constexpr int TILE = 4096;
+  constexpr int NBUF = 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  float2* ibuf = reinterpret_cast<float2*>(smem_raw + 128);
+  float2* xbuf = ibuf + NBUF * TILE;
+  const int tid = threadIdx.x;
+  const int t = tid % T, u = tid / T;  // lanes across transforms
+  const int64_t ntiles = (k.V0 + T - 1) / T;
+  if (tid == 0) {
+    for (int b = 0; b < NBUF; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int b, int64_t tile) {
+    const int64_t c0 = tile * T;
+    const int64_t cnt = (k.V0 - c0) < T ? (k.V0 - c0) : T;
+    const uint32_t bar = smem_addr(bars + b);
+    expect_tx(bar, (uint32_t)(cnt * C::N * 8));
+    bulk_copy(smem_addr(ibuf + b * TILE), k.in + c0 * C::N, (uint32_t)(cnt * C::N * 8), bar);
+  };
+  if (tid == 0)
+    for (int b = 0; b < NBUF; ++b) {
+      const int64_t tile = blockIdx.x + (int64_t)b * gridDim.x;
+      if (tile < ntiles) issue(b, tile);
+    }
+  float2 v[16];
+  float2* xrow = xbuf + t * C::PITCH;
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it % NBUF;
+    const bool ok = mbar_wait(smem_addr(bars + b), (uint32_t)((it / NBUF) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
+      return;
+    }
+    const int64_t c0 = tile * T;
+    const int cnt = (int)((k.V0 - c0) < T ? (k.V0 - c0) : T);
+    // re-layout: 128-bit reads of the landed tile into odd-pitch rows
+    const float4* src4 = reinterpret_cast<const float4*>(ibuf + b * TILE);
+    for (int i = tid; i < TILE / 2; i += 256) {
+      float4 w = src4[i];
+      if (k.conj) {
+        w.y = -w.y;
+        w.w = -w.w;
+      }
+      const int e = 2 * i, tt = e >> LOGN, p = e & (C::N - 1);
+      xbuf[tt * C::PITCH + phys(p)] = make_float2(w.x, w.y);
+      xbuf[tt * C::PITCH + phys(p + 1)] = make_float2(w.z, w.w);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int64_t next = tile + (int64_t)NBUF * gridDim.x;
+      if (next < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(b, next);
+      }
+    }
+    stage_in<LOGN, 0, false, 1>(v, xrow, k.twt, u, 0);
+    __syncthreads();
+    stage_out_x<LOGN, 0>(v, xrow, u);
+    __syncthreads();
+    if constexpr (C::NST > 1) {
+      static_assert(C::NST == 2, "small kernel covers two stages at most");
+      stage_in<LOGN, 1, false, 1>(v, xrow, k.twt, u, 0);
+      __syncthreads();
+      stage_out_x<LOGN, 1>(v, xrow, u);
+      __syncthreads();
+    }
+    // 128-bit stores of the rows, transforms adjacent in the output
+    float4* dst4 = reinterpret_cast<float4*>(k.out + c0 * C::N);
+    for (int i = tid; i < cnt * C::N / 2; i += 256) {
+      const int e = 2 * i, tt = e >> LOGN, p = e & (C::N - 1);
+      const float2 a = xbuf[tt * C::PITCH + phys(p)], c = xbuf[tt * C::PITCH + phys(p + 1)];
+      dst4[i] = k.conj ? make_float4(a.x, -a.y, c.x, -c.y) : make_float4(a.x, a.y, c.x, c.y);
+    }
+    __syncthreads();  // rows read out before the next tile's re-layout
+  }
+}
+
+template <int LOGN>
+cudaError_t launch_small(const GbP2& k, cudaStream_t st) {
+  using C = P2<LOGN>;
+  constexpr int T = 4096 / C::N;
+  const size_t smem = 128 + sizeof(float2) * (2 * 4096 + (size_t)T * C::PITCH);
+  auto fn = gb_p2small_kernel<LOGN>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = (k.V0 + T - 1) / T;
+  int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  if (k.grid > 0) grid = k.grid;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) return cudaSuccess;
+  fn<<<(unsigned)grid, 256, smem, st>>>(k);
+  return cudaGetLastError();
+}
+
 // transforms per CTA tile, by size and tile shape (tiles of 32-64 KB)
 constexpr int tile_T(int logn, int load, int store) {
   return (load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG)
@@ -387,8 +501,16 @@ template <int LOAD, int STORE, bool POSTTW>
 cudaError_t dispatch(const GbP2& k, cudaStream_t st) {
   constexpr bool cc = LOAD == GB_P2_LOAD_CONTIG && STORE == GB_P2_STORE_CONTIG;
   switch (k.logn) {
-    case 6: if constexpr (!cc) return launch_n<6, LOAD, STORE, POSTTW>(k, st); break;
-    case 7: if constexpr (!cc) return launch_n<7, LOAD, STORE, POSTTW>(k, st); break;
+    case 4: if constexpr (cc && !POSTTW) return launch_small<4>(k, st); break;
+    case 5: if constexpr (cc && !POSTTW) return launch_small<5>(k, st); break;
+    case 6:
+      if constexpr (cc && !POSTTW) return launch_small<6>(k, st);
+      else if constexpr (!cc) return launch_n<6, LOAD, STORE, POSTTW>(k, st);
+      break;
+    case 7:
+      if constexpr (cc && !POSTTW) return launch_small<7>(k, st);
+      else if constexpr (!cc) return launch_n<7, LOAD, STORE, POSTTW>(k, st);
+      break;
     case 8: return launch_n<8, LOAD, STORE, POSTTW>(k, st);
     case 9: return launch_n<9, LOAD, STORE, POSTTW>(k, st);
     case 10: return launch_n<10, LOAD, STORE, POSTTW>(k, st);
@@ -404,7 +526,7 @@ cudaError_t dispatch(const GbP2& k, cudaStream_t st) {
 
 int gb_p2_supported(int logn, int load, int store, int posttw) {
   const bool cc = load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG;
-  if (cc) return !posttw && logn >= 8 && logn <= 13;
+  if (cc) return !posttw && logn >= 4 && logn <= 13;
   if (logn < 6 || logn > 12) return 0;
   if (posttw && !(load == GB_P2_LOAD_ROWS && store == GB_P2_STORE_COLS)) return 0;
   if (posttw && logn % 4 != 0 && logn / 4 + 1 < 2) return 0;
@@ -412,6 +534,9 @@ int gb_p2_supported(int logn, int load, int store, int posttw) {
 }
 
 int gb_p2_tile(int logn, int load, int store) { return tile_T(logn, load, store); }
+
+// the small-transform kernel needs adjacent transforms on both sides
+int gb_p2_small(int logn) { return logn >= 4 && logn <= 7; }
 
 int gb_p2_twiddle_elems(int logn) {
   const int rem = logn % 4, r0 = rem ? (1 << rem) : 16, nst = logn / 4 + (rem ? 1 : 0);

@@ -257,3 +257,14 @@ def test_p2_strided_tile_shapes():
     x = u(1024 * 20, 61)
     err, info = check([(1024, 1, 20)], [(20, 1024, 1)], -1, x, flags=EST)
     assert "p2-tma" not in info and "pass stockham" in info
+
+
+@pytest.mark.parametrize("e", [4, 5, 6, 7])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_small_transform_kernel(e, sign):
+    """n = 16..128: the tile is re-laid into odd-pitch rows; ragged last tile."""
+    n = 2 ** e
+    b = (4096 // n) * 5 + 3
+    x = u(n * b, 70 + e)
+    err, info = check([(n, 1, 1)], [(b, n, n)], sign, x, flags=EST)
+    assert "p2-tma" in info
