@@ -339,8 +339,109 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_uneven(args):
+    """The uneven-batch workload (sizes 1000, 2187, 3125, 7168, 10007, 65536 x 512,
+    contiguous and transposed layouts) as one persistent group launch, and the
+    same plans executed one after another, on one GPU."""
+    import torch
+
+    from paper_2602_23525_gb300 import gbfft
+    batch = fft_inputs.UNEVEN_BATCH
+    plans, ins, outs, flops = [], [], [], 0.0
+    for i, n in enumerate(fft_inputs.UNEVEN_SIZES):
+        dims, how = (fft_inputs.transposed_1d(n, batch) if n in fft_inputs.UNEVEN_TRANSPOSED
+                     else fft_inputs.batched_1d(n, batch))
+        plans.append(gbfft.Plan(dims, how, -1, gbfft.FFT_ESTIMATE if args.estimate else gbfft.FFT_MEASURE))
+        x = torch.from_numpy(fft_inputs.gaussian_c64(n * batch, fft_inputs.seed_for(2, i))).cuda()
+        ins.append(x)
+        outs.append(torch.empty_like(x))
+        flops += flops_of(n, batch)
+    g = gbfft.fft_group_create([p.handle for p in plans])
+    s = torch.cuda.Stream()
+    sp = s.cuda_stream
+    ip, op = [t.data_ptr() for t in ins], [t.data_ptr() for t in outs]
+
+    def timed(fn):
+        with torch.cuda.stream(s):
+            for _ in range(args.warmup):
+                fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            for _ in range(args.steps):
+                fn()
+            b.record(s)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
+    t_group = timed(lambda: gbfft.fft_group_execute(g, ip, op, sp))
+    t_seq = timed(lambda: [gbfft.fft_execute(p.handle, i, o, sp) for p, i, o in zip(plans, ip, op)])
+    status = gbfft.fft_group_status(g)
+    nbytes = sum(16.0 * n * batch for n in fft_inputs.UNEVEN_SIZES)
+    res = {"metric": METRIC, "workload": "uneven: sizes 1000, 2187, 3125, 7168, 10007, 65536 x 512, "
+           "2187/7168/65536 transposed, forward, one persistent launch", "unit": "GFLOP/s",
+           "group": {"ms": round(t_group, 4), "value": round(flops / (t_group * 1e-3) / 1e9, 1),
+                     "gbs_algorithmic": round(nbytes / (t_group * 1e-3) / 1e9, 1), "launches": 1,
+                     "status": status},
+           "sequential": {"ms": round(t_seq, 4), "value": round(flops / (t_seq * 1e-3) / 1e9, 1),
+                          "gbs_algorithmic": round(nbytes / (t_seq * 1e-3) / 1e9, 1),
+                          "launches": sum(p.launches for p in plans)},
+           "plans": [p.info for p in plans]}
+    gbfft.fft_group_destroy(g)
+    return res
+
+
+def run_serving(args):
+    """The serving workload: requests of mixed shapes (rank 1-3), batches and signs
+    with Poisson arrivals, admitted by a 40 GB work-buffer budget.  The arrival
+    rate is 70% of the closed-loop capacity measured on the first requests.
+    Host buffers are pinned; requests share one input and one output pool."""
+    import torch
+
+    from paper_2602_23525_gb300 import gbfft
+    reqs = fft_inputs.serving_requests(args.requests, fft_inputs.seed_for(5))
+    max_elems = max(int(np.prod(sh)) * b for sh, b, _ in reqs)
+    pool_in = torch.from_numpy(fft_inputs.uniform_c64(max_elems, fft_inputs.seed_for(5, 1))).pin_memory()
+    pool_out = torch.empty_like(pool_in).pin_memory()
+    pin, pout = pool_in.data_ptr(), pool_out.data_ptr()
+
+    def run(subset, rate):
+        server = gbfft.fft_server_create(fft_inputs.SERVING_BUDGET, args.streams)
+        t_start = gbfft.fft_server_now(server)
+        arrivals = (fft_inputs.poisson_arrivals(len(subset), rate, fft_inputs.seed_for(5, 2))
+                    if rate else np.zeros(len(subset)))
+        for (shape, batch, sign), at in zip(subset, arrivals):
+            when = t_start + float(at)
+            while rate and gbfft.fft_server_now(server) < when:
+                d = when - gbfft.fft_server_now(server)
+                if d > 2e-4:
+                    time.sleep(d - 1e-4)
+            gbfft.fft_server_submit(server, shape, batch, sign, pin, pout, when)
+        gbfft.fft_server_drain(server, 3600.0)
+        st = gbfft.fft_server_stats(server)
+        gbfft.fft_server_destroy(server)
+        return st
+
+    calib = reqs[: max(1, min(len(reqs), args.requests // 10))]
+    run(calib[: min(50, len(calib))], 0)  # warm the caches the loop does not own (first plans, context)
+    closed = run(calib, 0)
+    rate = args.rate if args.rate else 0.7 * closed["requests_per_s"]
+    open_ = run(reqs, rate)
+    return {"metric": METRIC, "workload": "serving: %d requests, Poisson arrivals at %.1f/s (0.7 x closed-loop "
+            "capacity %.1f/s), n 2^6..2^20 (80%%) or non-power-of-two 100..1e5, rank 1/2/3, batch 1..256, "
+            "sign +-1, 40 GB budget, %d streams" % (len(reqs), rate, closed["requests_per_s"], args.streams),
+            "unit": "s", "p50_latency_s": open_["p50_latency_s"], "p99_latency_s": open_["p99_latency_s"],
+            "throughput_gflops": open_["gflops"], "throughput_requests_per_s": open_["requests_per_s"],
+            "higher_is_better": False, "open_loop": open_, "closed_loop": closed,
+            "host_buffers": "pinned, shared pools (inputs read from one pool, outputs written to one pool)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "uneven", "serving"],
+                    help="sweep: the benchmark step; uneven / serving: extra workloads (their own line)")
+    ap.add_argument("--requests", type=int, default=100000, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: 0.7 x capacity)")
+    ap.add_argument("--streams", type=int, default=4, help="serving: streams")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -354,6 +455,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     args.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload in ("uneven", "serving"):
+        if rank == 0:
+            fn = run_uneven if args.workload == "uneven" else run_serving
+            print(json.dumps(fn(args)), flush=True)
+        return
     if args.impl == "reference":
         res = run_reference(args, rank, world)
         if res is not None:

@@ -70,6 +70,7 @@ enum {
 #define FFT_ESTIMATE (1u << 0)     /* heuristic plan, no timing (sec. 4.3, "estimate mode") */
 #define FFT_WISDOM_ONLY (1u << 1)  /* use only imported wisdom; fail otherwise */
 #define FFT_INPLACE (1u << 2)      /* executed with in == out; requires is == os everywhere */
+#define FFT_EXTERNAL_SCRATCH (1u << 3) /* no plan-owned scratch: pass a work area to fft_execute_scratch */
 #define FFT_PREC_TC_FP16 (1u << 4) /* radix-16 stages as FP16 tensor-core MMAs */
 #define FFT_PREC_TC_BF16 (1u << 5) /* radix-16 stages as BF16 tensor-core MMAs */
 #define FFT_PREC_SPLIT (1u << 6)   /* with a TC flag: split hi+lo operands */
@@ -109,6 +110,17 @@ fft_plan fft_plan_dft(int rank, const fft_iodim *dims, int howmany_rank,
  */
 int fft_execute(fft_plan p, const void *in, void *out, void *stream);
 
+/*
+ * fft_execute_scratch -- run a plan made with FFT_EXTERNAL_SCRATCH, using the
+ * caller's device work area `scratch` (256-byte aligned, at least
+ * fft_plan_scratch_bytes(p) bytes; may be NULL when that is 0) instead of
+ * plan-owned scratch, so that one plan can run concurrently on several
+ * streams with separate work areas.  Otherwise as fft_execute; plans with
+ * external scratch must be run with this call (fft_execute returns
+ * FFT_ERR_INVALID_ARG for them when they need scratch).
+ */
+int fft_execute_scratch(fft_plan p, const void *in, void *out, void *scratch, void *stream);
+
 /* fft_destroy -- free a plan and its device memory; NULL is ignored.  The
  * caller must make sure no enqueued execution of the plan is still running. */
 void fft_destroy(fft_plan p);
@@ -144,7 +156,8 @@ double fft_plan_flops(fft_plan p);
 /* Number of kernel launches one fft_execute enqueues. */
 int fft_plan_launches(fft_plan p);
 
-/* Device scratch bytes the plan holds (excludes twiddle tables). */
+/* Device scratch bytes the plan holds, or (FFT_EXTERNAL_SCRATCH) needs in the
+ * caller's work area; excludes twiddle tables. */
 size_t fft_plan_scratch_bytes(fft_plan p);
 
 /* ---------------------------------------------------------------- wisdom */
@@ -161,6 +174,81 @@ size_t fft_plan_scratch_bytes(fft_plan p);
 int fft_export_wisdom(char *buf, size_t len);
 int fft_import_wisdom(const char *text);
 void fft_forget_wisdom(void);
+
+/* ---------------------------------------------------------------- groups */
+
+/*
+ * Uneven batches in one persistent launch.  A group holds several plans of
+ * any kind and executes all of them together: one persistent kernel takes
+ * (step, tile) work items from a device queue ordered by step level, each
+ * item waiting (bounded, about 1 s) until the previous step of its own plan
+ * has completed; a plan's power-of-two pass kernels are replaced there by its
+ * generic pass over the same sub-problem, so each transform's result matches
+ * executing its plan alone to within the library's rounding (not bit for bit).
+ *   fft_group_create  : nplans >= 1 plans, kept by pointer (they must outlive
+ *                       the group); flags 0 or FFT_GROUP_DEBUG_STALL.  NULL on
+ *                       error (INVALID_ARG, UNSUPPORTED, OOM, CUDA).
+ *   fft_group_execute : ins[i], outs[i] are the device arrays of plan i, with
+ *                       the same rules as fft_execute.  On a non-default
+ *                       stream the launch (counter reset + kernel) is captured
+ *                       into a CUDA graph once and replayed afterwards; the
+ *                       pointer table is rewritten only when pointers change.
+ *                       Executions of one group must not overlap on the GPU.
+ *   fft_group_status  : waits for the device, returns FFT_OK or
+ *                       FFT_ERR_DEVICE_TIMEOUT if a wait gave up (and clears it).
+ *   fft_group_launches: kernel launches per execution (1).
+ * FFT_GROUP_DEBUG_STALL adds one work item that waits on a segment no item
+ * belongs to, with a 50 ms bound: for testing that a device wait that runs
+ * out reports FFT_ERR_DEVICE_TIMEOUT and leaves the context usable.
+ * The persistent executor has no counterpart in the paper; it serves the
+ * vector loops of sec. 4.1 when the transforms of a batch differ in size.
+ */
+#define FFT_GROUP_DEBUG_STALL (1u << 8)
+typedef struct fft_group_s *fft_group;
+fft_group fft_group_create(int nplans, const fft_plan *plans, unsigned flags);
+int fft_group_execute(fft_group g, const void *const *ins, void *const *outs, void *stream);
+int fft_group_status(fft_group g);
+int fft_group_launches(fft_group g);
+void fft_group_destroy(fft_group g);
+
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * A continuous-batching request loop (no counterpart in the paper; it serves
+ * many independent problems of sec. 4.1 as they arrive).  Requests are dense
+ * row-major transforms: rank in [1, 3], lengths n[0..rank-1] (last index
+ * fastest), `batch` transforms back to back, sign -1/+1, with HOST input and
+ * output buffers (pinned memory gives asynchronous copies).  A worker thread
+ * admits waiting requests in arrival order whenever their device work buffers
+ * (input, output and plan scratch, carved from one pool of `budget_bytes`) fit
+ * in the unused budget and one of `nstreams` streams has a free slot; waiting
+ * requests with the same shape and sign are merged into one launch.  Copies and
+ * transforms of different launches overlap on the device.  Plans stay cached.
+ *   fft_server_create : budget_bytes >= 4096, nstreams in [1, 64], flags 0;
+ *                       allocates the pool on the current device.
+ *   fft_server_submit : enqueues; `arrival` is the request's arrival time in
+ *                       seconds on the server clock (fft_server_now), or < 0
+ *                       for "now"; *ticket identifies it.  The host buffers
+ *                       must stay valid until the request completes.
+ *   fft_server_poll   : FFT_OK when done, 1 while queued or running, else the
+ *                       request's error (FFT_ERR_BUDGET if it can never fit).
+ *   fft_server_wait   : like poll, blocking up to timeout_s seconds.
+ *   fft_server_drain  : waits until nothing is queued or running (1 on timeout).
+ *   fft_server_stats  : JSON text (completed, launches, merged requests, p50 /
+ *                       p99 latency from arrival to completion, throughput,
+ *                       budget high-water mark); length as fft_plan_info.
+ *   fft_server_destroy: finishes queued work, then frees everything.
+ */
+typedef struct fft_server_s *fft_server;
+fft_server fft_server_create(size_t budget_bytes, int nstreams, unsigned flags);
+double fft_server_now(fft_server s);
+int fft_server_submit(fft_server s, int rank, const int64_t *n, int64_t batch, int sign,
+                      const void *host_in, void *host_out, double arrival, uint64_t *ticket);
+int fft_server_poll(fft_server s, uint64_t ticket);
+int fft_server_wait(fft_server s, uint64_t ticket, double timeout_s);
+int fft_server_drain(fft_server s, double timeout_s);
+int fft_server_stats(fft_server s, char *buf, size_t len);
+void fft_server_destroy(fft_server s);
 
 /* ---------------------------------------------------------------- no allocation */
 

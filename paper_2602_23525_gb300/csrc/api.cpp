@@ -96,8 +96,15 @@ int fft_plan_explain(int rank, const fft_iodim* dims, int howmany_rank, const ff
 
 int fft_execute(fft_plan p, const void* in, void* out, void* stream) {
   if (!p) return set_err(FFT_ERR_INVALID_ARG);
+  if (p->d.external_scratch && !p->d.scratch.empty()) return set_err(FFT_ERR_INVALID_ARG);
   const int rc = execute_plan(&p->d, in, out, (cudaStream_t)stream);
   return set_err(rc);
+}
+
+int fft_execute_scratch(fft_plan p, const void* in, void* out, void* scratch, void* stream) {
+  if (!p) return set_err(FFT_ERR_INVALID_ARG);
+  if (!p->d.external_scratch) return set_err(FFT_ERR_INVALID_ARG);
+  return set_err(execute_plan(&p->d, in, out, (cudaStream_t)stream, scratch));
 }
 
 void fft_destroy(fft_plan p) {
@@ -121,7 +128,7 @@ int fft_plan_launches(fft_plan p) { return p ? (int)p->d.steps.size() : 0; }
 size_t fft_plan_scratch_bytes(fft_plan p) {
   if (!p) return 0;
   size_t s = 0;
-  for (size_t b : p->d.scratch_bytes) s += b;
+  for (size_t b : p->d.scratch_bytes) s += (b + 255) & ~(size_t)255;
   return s;
 }
 

@@ -11,65 +11,29 @@
 #include <cuda_runtime.h>
 
 #include "gb_kernels.h"
+#include "gb_pointwise.cuh"
 
 namespace {
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-__device__ __forceinline__ void vec_offsets(const GbBlueIO& b, int64_t v, int64_t* io, int64_t* oo) {
-  int64_t a = 0, c = 0;
-  for (int d = b.nv - 1; d >= 0; --d) {
-    const int64_t q = v / b.vn[d];
-    const int64_t i = v - q * b.vn[d];
-    v = q;
-    a += i * b.vis[d];
-    c += i * b.vos[d];
-  }
-  *io = a;
-  *oo = c;
-}
 
 __global__ void gb_blue_pre_kernel(const GbBlueIO b) {
   const int64_t total = b.count * b.m;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int64_t v = i / b.m, l = i - (i / b.m) * b.m;
-    float2 val = make_float2(0.f, 0.f);
-    if (l < b.n) {
-      int64_t io, oo;
-      vec_offsets(b, v, &io, &oo);
-      float2 x = __ldg(b.in + io + l * b.is);
-      if (b.conj) x.y = -x.y;
-      val = cmul(x, __ldg(b.w + l));
-    }
-    b.work[i] = val;
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
+    gb_blue_pre_elem(b, b.in, b.work, i, 0);
 }
 
 __global__ void gb_blue_mul_kernel(const GbBlueIO b, float2* data) {
   const int64_t total = b.count * b.m;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const float2 z = cmul(data[i], __ldg(b.B + i % b.m));
-    data[i] = make_float2(z.x, -z.y);
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
+    gb_blue_mul_elem(b, data, i);
 }
 
 __global__ void gb_blue_post_kernel(const GbBlueIO b, const float2* data) {
   const int64_t total = b.count * b.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int64_t v = i / b.n, k = i - (i / b.n) * b.n;
-    int64_t io, oo;
-    vec_offsets(b, v, &io, &oo);
-    float2 d = data[v * b.m + k];
-    d.y = -d.y;
-    float2 y = cmul(d, __ldg(b.w + k));
-    if (b.conj) y.y = -y.y;
-    b.out[oo + k * b.os] = y;
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
+    gb_blue_post_elem(b, data, b.out, i);
 }
 
 unsigned grid_for(int64_t count) {

@@ -120,7 +120,12 @@ struct Builder {
   int new_scratch(size_t bytes) {
     const int id = BUF_SCRATCH0 + (int)P->scratch.size();
     void* ptr = nullptr;
-    if (device && !err) {
+    if (P->external_scratch) {
+      // carved from the caller's work area at execute time, 256-byte aligned
+      size_t off = 0;
+      for (size_t b : P->scratch_bytes) off += (b + 255) & ~(size_t)255;
+      P->scratch_offset.push_back(off);
+    } else if (device && !err) {
       if (cudaMalloc(&ptr, bytes ? bytes : 16) != cudaSuccess) {
         cudaGetLastError();
         err = FFT_ERR_OOM;
@@ -482,7 +487,7 @@ struct Builder {
       }
       if (gb_make_chirp(w, n, 0) != cudaSuccess ||
           gb_make_bluestein_kernel(B, n, m, rad.data(), (int)rad.size(), work, 0) != cudaSuccess ||
-          cudaDeviceSynchronize() != cudaSuccess)
+          cudaStreamSynchronize(0) != cudaSuccess)
         err = FFT_ERR_CUDA;
       cudaFree(work);
     }
@@ -860,11 +865,13 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
   return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
 }
 
-static int run_steps(PlanData* p, const void* in, void* out, cudaStream_t st) {
+static int run_steps(PlanData* p, const void* in, void* out, cudaStream_t st, void* work = nullptr) {
   std::vector<float2*> bufs(BUF_SCRATCH0 + p->scratch.size());
   bufs[BUF_IN] = (float2*)in;
   bufs[BUF_OUT] = (float2*)out;
-  for (size_t k = 0; k < p->scratch.size(); ++k) bufs[BUF_SCRATCH0 + k] = (float2*)p->scratch[k];
+  for (size_t k = 0; k < p->scratch.size(); ++k)
+    bufs[BUF_SCRATCH0 + k] =
+        p->external_scratch ? (float2*)((char*)work + p->scratch_offset[k]) : (float2*)p->scratch[k];
   for (const Step& s : p->steps) {
     const int rc = launch_step(s, bufs.data(), st);
     if (rc != FFT_OK) return rc;
@@ -941,6 +948,7 @@ double Builder::time_choice(const Dim& d, const std::vector<Dim>& Vin, bool inpl
 int build_plan(const Problem& P, bool device, PlanData* out) {
   out->prob = P;
   out->inplace = (P.flags & FFT_INPLACE) != 0;
+  out->external_scratch = (P.flags & FFT_EXTERNAL_SCRATCH) != 0;
   std::ostringstream head;
   head << "dft rank=" << P.N.size() << " n=" << dims_str(P.N) << " howmany=" << dims_str(P.V)
        << " sign=" << P.sign << (out->inplace ? " in-place" : "") << ((P.flags & FFT_ESTIMATE) ? " estimate" : "")
@@ -971,7 +979,7 @@ int build_plan(const Problem& P, bool device, PlanData* out) {
   Builder b(out, device, measure, (P.flags & FFT_WISDOM_ONLY) != 0);
   const int conj = P.sign > 0 ? 1 : 0;
   b.solve(P.N, P.V, BUF_IN, out->inplace ? BUF_IN : BUF_OUT, conj, 1);
-  if (!b.err && device && cudaDeviceSynchronize() != cudaSuccess) b.err = FFT_ERR_CUDA;
+  if (!b.err && device && cudaStreamSynchronize(0) != cudaSuccess) b.err = FFT_ERR_CUDA;
   out->info = head.str() + b.info.str();
   if (b.err) {
     release(out);
@@ -980,7 +988,7 @@ int build_plan(const Problem& P, bool device, PlanData* out) {
   return FFT_OK;
 }
 
-int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st) {
+int check_execute_args(const PlanData* p, const void* in, const void* out) {
   if (p->prob.empty) return FFT_OK;
   if (!in || !out) return FFT_ERR_INVALID_ARG;
   if (p->inplace) {
@@ -992,7 +1000,16 @@ int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st) {
     const char* b1 = (const char*)out + 8 * (p->out_hi + 1);
     if (a0 < b1 && b0 < a1) return FFT_ERR_ALIAS;
   }
-  return run_steps(p, in, p->inplace ? (void*)in : out, st);
+  return FFT_OK;
+}
+
+int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st, void* work) {
+  if (p->prob.empty) return FFT_OK;
+  const int rc = check_execute_args(p, in, out);
+  if (rc != FFT_OK) return rc;
+  if (p->external_scratch && !p->scratch.empty() && (!work || ((uintptr_t)work & 255)))
+    return FFT_ERR_INVALID_ARG;
+  return run_steps(p, in, p->inplace ? (void*)in : out, st, work);
 }
 
 }  // namespace gb

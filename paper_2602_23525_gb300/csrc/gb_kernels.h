@@ -57,6 +57,34 @@ cudaError_t gb_launch_blue_pre(const GbBlueIO& b, cudaStream_t st);     // work 
 cudaError_t gb_launch_blue_mul(const GbBlueIO& b, float2* data, cudaStream_t st);  // data = conj(data Bhat)
 cudaError_t gb_launch_blue_post(const GbBlueIO& b, const float2* data, cudaStream_t st);  // y = w conj(data)
 
+// Persistent executor of several plans in one launch (stockham.cu).  Work
+// items are (segment, tile); a segment is one step of one plan and may wait
+// for the segment holding the previous step of the same plan.
+enum { GB_SEG_PASS = 0, GB_SEG_COPY = 1, GB_SEG_BLUE_PRE = 2, GB_SEG_BLUE_MUL = 3, GB_SEG_BLUE_POST = 4 };
+#define GB_SEG_CHUNK 4096  // elements per item of an element-wise segment
+struct GbGroupSeg {
+  int kind;
+  int src, dst;          // slots of the per-execution pointer table
+  int dep;               // segment that must complete first, or -1
+  const GbPass* pass;    // GB_SEG_PASS: device descriptor
+  GbBlueIO blue;         // Bluestein element-wise segments (pointers come from slots)
+  GbCopy copy;           // GB_SEG_COPY
+  int64_t ntiles;        // work items of the segment
+  int64_t first;         // global index of its first item
+};
+struct GbGroupArgs {
+  const GbGroupSeg* segs;
+  int nseg;
+  float2* const* bufs;          // pointer table
+  unsigned long long* head;     // next item to hand out
+  unsigned long long* done;     // completed items per segment
+  int64_t total;                // items in the queue
+  int* status;                  // FFT_ERR_DEVICE_TIMEOUT when a wait gives up
+  unsigned long long wait_ns;   // bound of every dependency wait
+};
+cudaError_t gb_launch_group(const GbGroupArgs& a, int threads, size_t smem, int64_t grid, cudaStream_t st);
+int gb_group_grid(int threads, size_t smem);
+
 // FP64 table generation (tables.cu).
 cudaError_t gb_make_roots(float2* out, int64_t count, int64_t N, int64_t mult, cudaStream_t st);
 cudaError_t gb_make_chirp(float2* out, int64_t n, cudaStream_t st);

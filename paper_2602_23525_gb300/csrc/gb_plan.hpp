@@ -60,6 +60,8 @@ struct PlanData {
   std::vector<void*> tables;   // device memory owned by the plan
   std::vector<void*> scratch;  // scratch buffers (ids BUF_SCRATCH0 + k)
   std::vector<size_t> scratch_bytes;
+  std::vector<size_t> scratch_offset;  // external scratch: offsets in the caller's work area
+  bool external_scratch = false;
   int* d_status = nullptr;
   std::string info;
   double bytes = 0.0, flops = 0.0;
@@ -92,7 +94,8 @@ void wisdom_put(const std::string& key, const std::string& val);
 // text only (no allocation, no timing).  Returns an FFT_* code.
 int build_plan(const Problem& P, bool device, PlanData* out);
 void free_plan(PlanData* p);
-int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st);
+int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st, void* work = nullptr);
+int check_execute_args(const PlanData* p, const void* in, const void* out);
 int launch_step(const Step& s, float2* const* bufs, cudaStream_t st);
 
 }  // namespace gb

@@ -61,7 +61,7 @@ std::string dims_str(const std::vector<Dim>& v) {
   return o.str();
 }
 
-static const unsigned kKnownFlags = FFT_ESTIMATE | FFT_WISDOM_ONLY | FFT_INPLACE | FFT_PREC_TC_FP16 |
+static const unsigned kKnownFlags = FFT_ESTIMATE | FFT_WISDOM_ONLY | FFT_INPLACE | FFT_EXTERNAL_SCRATCH | FFT_PREC_TC_FP16 |
                                     FFT_PREC_TC_BF16 | FFT_PREC_SPLIT;
 
 int canonicalize(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, int sign,

@@ -14,6 +14,7 @@
 #include "codelets.cuh"
 #include "gb_kernels.h"
 #include "gb_pass.h"
+#include "gb_pointwise.cuh"
 
 namespace {
 
@@ -26,8 +27,8 @@ __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.
 // padded shared-memory index: one pad element per 32, breaks power-of-two bank strides
 __device__ __forceinline__ int phys(int i) { return i + (i >> 5); }
 
-__device__ __forceinline__ float2 load_c(const float2* p, int conj) {
-  float2 v = __ldg(p);
+__device__ __forceinline__ float2 load_c(const float2* p, int conj, int coherent = 0) {
+  float2 v = coherent ? __ldcg(p) : __ldg(p);
   if (conj) v.y = -v.y;
   return v;
 }
@@ -60,6 +61,7 @@ template <> __device__ __forceinline__ void codelet<16>(float2* v) { gb_dft16(v)
 struct TileCtx {
   const float2* in;  // pass input, element 0
   float2* out;       // pass output, element 0
+  int coherent;      // 1: data may have been written earlier in this launch (load through L2)
   int t, u;          // transform within the tile, thread within the transform
   bool tvalid;       // this thread's transform exists
   int64_t bin, bout; // element offsets of this thread's transform
@@ -84,7 +86,7 @@ __device__ __forceinline__ void stage(const GbPass& p, int s, float2* sm, const 
       if (from_g) {
         const float2* src = c.in + c.bin;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b][r] = load_c(src + (int64_t)(j + r * nb) * p.is, p.conj);
+        for (int r = 0; r < R; ++r) v[b][r] = load_c(src + (int64_t)(j + r * nb) * p.is, p.conj, c.coherent);
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[b][r] = smt[phys(j + r * nb)];
@@ -169,12 +171,13 @@ __device__ __forceinline__ void tile_index(const GbPass& p, int idx, int order, 
   }
 }
 
-__device__ void tile_load(const GbPass& p, const float2* in, float2* sm, int64_t bin, int ntv) {
+__device__ void tile_load(const GbPass& p, const float2* in, float2* sm, int64_t bin, int ntv, int coherent) {
   const int total = p.T * p.n;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int t, e;
     tile_index(p, idx, p.load_copy, &t, &e);
-    if (t < ntv) sm[t * p.pitch + phys(e)] = load_c(in + bin + t * p.vis[0] + (int64_t)e * p.is, p.conj);
+    if (t < ntv)
+      sm[t * p.pitch + phys(e)] = load_c(in + bin + t * p.vis[0] + (int64_t)e * p.is, p.conj, coherent);
   }
 }
 
@@ -203,7 +206,8 @@ __device__ void bluestein_tile(const GbPass& p, float2* sm, const TileCtx& c, in
     const int t = idx / m, e = idx - (idx / m) * m;
     if (t < ntv) {
       float2 val = make_float2(0.f, 0.f);
-      if (e < p.bn) val = cmul(load_c(c.in + bin + t * p.vis[0] + (int64_t)e * p.is, p.conj), __ldg(p.bw + e));
+      if (e < p.bn)
+        val = cmul(load_c(c.in + bin + t * p.vis[0] + (int64_t)e * p.is, p.conj, c.coherent), __ldg(p.bw + e));
       sm[t * p.pitch + phys(e)] = val;
     }
   }
@@ -229,15 +233,15 @@ __device__ void bluestein_tile(const GbPass& p, float2* sm, const TileCtx& c, in
   __syncthreads();
 }
 
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT)
-    gb_stockham_kernel(const GbPass* __restrict__ P, const float2* in, float2* out) {
-  extern __shared__ float2 sm[];
-  const GbPass& p = *P;
+// One tile of a generic pass, computed by the whole CTA (any block size of at
+// least T * tpt threads; extra threads idle through the barriers).
+__device__ __forceinline__ void gb_pass_tile(const GbPass& p, const float2* in, float2* out, float2* sm, int64_t tile,
+                             int coherent) {
   const int tid = threadIdx.x;
   TileCtx c;
   c.in = in;
   c.out = out;
+  c.coherent = coherent;
   if (p.t_fast) {
     c.t = tid % p.T;
     c.u = tid / p.T;
@@ -245,48 +249,120 @@ __global__ void __launch_bounds__(MAXT)
     c.t = tid / p.tpt;
     c.u = tid - c.t * p.tpt;
   }
-  for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-    int64_t bin, bout, v0;
-    tile_origin(p, tile, &bin, &bout, &v0);
-    const int64_t left = p.vn[0] - v0;
-    const int ntv = left < p.T ? (int)left : p.T;
-    c.tvalid = c.t < ntv;
-    c.bin = bin + c.t * p.vis[0];
-    c.bout = bout + c.t * p.vos[0];
-    c.v0 = v0 + c.t;
-    if (p.blue) {
-      bluestein_tile(p, sm, c, bin, bout, ntv);
-      continue;
+  int64_t bin, bout, v0;
+  tile_origin(p, tile, &bin, &bout, &v0);
+  const int64_t left = p.vn[0] - v0;
+  const int ntv = left < p.T ? (int)left : p.T;
+  c.tvalid = c.t < ntv && c.u < p.tpt;
+  c.bin = bin + c.t * p.vis[0];
+  c.bout = bout + c.t * p.vos[0];
+  c.v0 = v0 + c.t;
+  if (p.blue) {
+    bluestein_tile(p, sm, c, bin, bout, ntv);
+    return;
+  }
+  if (p.load_mode == GB_MOVE_SMEM) {
+    tile_load(p, in, sm, bin, ntv, coherent);
+    __syncthreads();
+  }
+  for (int s = 0; s < p.nst; ++s) {
+    const bool from_g = (s == 0) && p.load_mode == GB_MOVE_DIRECT;
+    const bool to_g = (s == p.nst - 1) && p.store_mode == GB_MOVE_DIRECT;
+    run_stage(p, s, sm, c, from_g, to_g);
+  }
+  if (p.store_mode == GB_MOVE_SMEM) {
+    tile_store(p, out, sm, bout, v0, ntv);
+    __syncthreads();
+  }
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    gb_stockham_kernel(const GbPass* __restrict__ P, const float2* in, float2* out) {
+  extern __shared__ float2 sm[];
+  for (int64_t tile = blockIdx.x; tile < P->ntiles; tile += gridDim.x) gb_pass_tile(*P, in, out, sm, tile, 0);
+}
+
+// bounded wait until *p >= need (device scope), by %globaltimer
+__device__ __forceinline__ bool wait_count(const unsigned long long* p, unsigned long long need,
+                                           unsigned long long limit_ns) {
+  if (*(volatile const unsigned long long*)p >= need) return true;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    if (*(volatile const unsigned long long*)p >= need) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > limit_ns) return false;
+    __nanosleep(200);
+  }
+}
+
+// Persistent executor: each CTA takes the next item of a device queue ordered
+// by step level (every dependency comes earlier in the queue, so a waiting
+// CTA only waits for items already taken by running CTAs), waits until the
+// segment it depends on has completed, runs the item and counts it done.
+// Data written earlier in the same launch is read through L2 (coherent).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT) gb_group_kernel(const __grid_constant__ GbGroupArgs a) {
+  extern __shared__ float2 sm[];
+  __shared__ long long s_item;
+  __shared__ int s_fail;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.head, 1ull);
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= a.total) return;
+    int s = 0;
+    while (s + 1 < a.nseg && a.segs[s + 1].first <= item) ++s;
+    const GbGroupSeg& g = a.segs[s];
+    if (threadIdx.x == 0) {
+      int fail = 0;
+      if (g.dep >= 0 && !wait_count(a.done + g.dep, (unsigned long long)a.segs[g.dep].ntiles, a.wait_ns)) fail = 1;
+      __threadfence();
+      s_fail = fail;
     }
-    if (p.load_mode == GB_MOVE_SMEM) {
-      tile_load(p, in, sm, bin, ntv);
-      __syncthreads();
+    __syncthreads();
+    if (s_fail) {
+      if (threadIdx.x == 0 && a.status) atomicExch(a.status, 8);  // FFT_ERR_DEVICE_TIMEOUT
+      return;
     }
-    for (int s = 0; s < p.nst; ++s) {
-      const bool from_g = (s == 0) && p.load_mode == GB_MOVE_DIRECT;
-      const bool to_g = (s == p.nst - 1) && p.store_mode == GB_MOVE_DIRECT;
-      run_stage(p, s, sm, c, from_g, to_g);
+    const int64_t tile = item - g.first;
+    float2* src = a.bufs[g.src];
+    float2* dst = a.bufs[g.dst];
+    const int64_t i0 = tile * GB_SEG_CHUNK;
+    switch (g.kind) {
+      case GB_SEG_PASS:
+        gb_pass_tile(*g.pass, src, dst, sm, tile, 1);
+        break;
+      case GB_SEG_COPY:
+        for (int64_t i = i0 + threadIdx.x; i < i0 + GB_SEG_CHUNK && i < g.copy.total; i += blockDim.x)
+          gb_copy_elem(g.copy, src, dst, i, 1);
+        break;
+      case GB_SEG_BLUE_PRE:
+        for (int64_t i = i0 + threadIdx.x; i < i0 + GB_SEG_CHUNK && i < g.blue.count * g.blue.m; i += blockDim.x)
+          gb_blue_pre_elem(g.blue, src, dst, i, 1);
+        break;
+      case GB_SEG_BLUE_MUL:
+        for (int64_t i = i0 + threadIdx.x; i < i0 + GB_SEG_CHUNK && i < g.blue.count * g.blue.m; i += blockDim.x)
+          gb_blue_mul_elem(g.blue, dst, i);
+        break;
+      case GB_SEG_BLUE_POST:
+        for (int64_t i = i0 + threadIdx.x; i < i0 + GB_SEG_CHUNK && i < g.blue.count * g.blue.n; i += blockDim.x)
+          gb_blue_post_elem(g.blue, src, dst, i);
+        break;
+      default:
+        break;
     }
-    if (p.store_mode == GB_MOVE_SMEM) {
-      tile_store(p, out, sm, bout, v0, ntv);
-      __syncthreads();
-    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(a.done + s, 1ull);
   }
 }
 
 __global__ void gb_copy_kernel(const GbCopy c) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.total; i += stride) {
-    int64_t r = i, a = 0, b = 0;
-    for (int d = c.nv - 1; d >= 0; --d) {
-      const int64_t q = r / c.vn[d];
-      const int64_t k = r - q * c.vn[d];
-      r = q;
-      a += k * c.vis[d];
-      b += k * c.vos[d];
-    }
-    c.out[b] = __ldg(c.in + a);
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.total; i += stride)
+    gb_copy_elem(c, c.in, c.out, i, 0);
 }
 
 }  // namespace
@@ -316,6 +392,47 @@ cudaError_t gb_launch_pass(const GbPass& p, const GbPass* dev, const float2* in,
     e = cudaFuncSetAttribute(gb_stockham_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     gb_stockham_kernel<1024><<<(unsigned)grid, threads, smem, st>>>(dev, in, out);
+  }
+  return cudaGetLastError();
+}
+
+template <int MAXT>
+static int group_grid_for(size_t smem) {
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaFuncSetAttribute(gb_group_kernel<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gb_group_kernel<MAXT>, MAXT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+int gb_group_grid(int threads, size_t smem) {
+  if (threads <= 256) return group_grid_for<256>(smem);
+  if (threads <= 512) return group_grid_for<512>(smem);
+  return group_grid_for<1024>(smem);
+}
+
+cudaError_t gb_launch_group(const GbGroupArgs& a, int threads, size_t smem, int64_t grid, cudaStream_t st) {
+  if (a.total <= 0) return cudaSuccess;
+  if (grid > a.total) grid = a.total;
+  if (grid < 1) grid = 1;
+  cudaError_t e;
+  if (threads <= 256) {
+    e = cudaFuncSetAttribute(gb_group_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gb_group_kernel<256><<<(unsigned)grid, 256, smem, st>>>(a);
+  } else if (threads <= 512) {
+    e = cudaFuncSetAttribute(gb_group_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gb_group_kernel<512><<<(unsigned)grid, 512, smem, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(gb_group_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gb_group_kernel<1024><<<(unsigned)grid, 1024, smem, st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -35,9 +35,11 @@ FFT_MEASURE = 0
 FFT_ESTIMATE = 1 << 0
 FFT_WISDOM_ONLY = 1 << 1
 FFT_INPLACE = 1 << 2
+FFT_EXTERNAL_SCRATCH = 1 << 3
 FFT_PREC_TC_FP16 = 1 << 4
 FFT_PREC_TC_BF16 = 1 << 5
 FFT_PREC_SPLIT = 1 << 6
+FFT_GROUP_DEBUG_STALL = 1 << 8
 
 
 class fft_iodim(ctypes.Structure):
@@ -59,6 +61,8 @@ _SIGNATURES = {
                                        ctypes.POINTER(fft_iodim), ctypes.c_int, ctypes.c_uint]),
     "fft_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fft_destroy": (None, [ctypes.c_void_p]),
+    "fft_execute_scratch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
     "fft_last_error": (ctypes.c_int, []),
     "fft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fft_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
@@ -72,6 +76,22 @@ _SIGNATURES = {
     "fft_export_wisdom": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t]),
     "fft_import_wisdom": (ctypes.c_int, [ctypes.c_char_p]),
     "fft_forget_wisdom": (None, []),
+    "fft_group_create": (ctypes.c_void_p, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint]),
+    "fft_group_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "fft_group_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "fft_group_launches": (ctypes.c_int, [ctypes.c_void_p]),
+    "fft_group_destroy": (None, [ctypes.c_void_p]),
+    "fft_server_create": (ctypes.c_void_p, [ctypes.c_size_t, ctypes.c_int, ctypes.c_uint]),
+    "fft_server_now": (ctypes.c_double, [ctypes.c_void_p]),
+    "fft_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
+    "fft_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "fft_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
+    "fft_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "fft_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
+    "fft_server_destroy": (None, [ctypes.c_void_p]),
     "fft_execute_1d_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -139,6 +159,13 @@ def fft_execute(plan, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
         raise GbfftError(rc, "fft_execute")
 
 
+def fft_execute_scratch(plan, in_ptr: int, out_ptr: int, scratch_ptr: int, stream: int = 0) -> None:
+    rc = load().fft_execute_scratch(plan, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+                                    ctypes.c_void_p(scratch_ptr), ctypes.c_void_p(stream))
+    if rc != FFT_OK:
+        raise GbfftError(rc, "fft_execute_scratch")
+
+
 def fft_destroy(plan) -> None:
     if plan:
         load().fft_destroy(plan)
@@ -185,6 +212,84 @@ def fft_import_wisdom(text: str) -> None:
 
 def fft_forget_wisdom() -> None:
     load().fft_forget_wisdom()
+
+
+def _ptrs(vals):
+    arr = (ctypes.c_void_p * max(1, len(vals)))()
+    for i, v in enumerate(vals):
+        arr[i] = int(v)
+    return arr
+
+
+def fft_group_create(plans, flags=0):
+    """Group plan handles for one persistent launch; returns a handle or raises."""
+    g = load().fft_group_create(len(plans), _ptrs(plans), int(flags))
+    if not g:
+        raise GbfftError(fft_last_error(), "fft_group_create")
+    return g
+
+
+def fft_group_execute(group, in_ptrs, out_ptrs, stream=0) -> None:
+    rc = load().fft_group_execute(group, _ptrs(in_ptrs), _ptrs(out_ptrs), ctypes.c_void_p(stream))
+    if rc != FFT_OK:
+        raise GbfftError(rc, "fft_group_execute")
+
+
+def fft_group_status(group) -> int:
+    return load().fft_group_status(group)
+
+
+def fft_group_launches(group) -> int:
+    return load().fft_group_launches(group)
+
+
+def fft_group_destroy(group) -> None:
+    if group:
+        load().fft_group_destroy(group)
+
+
+def fft_server_create(budget_bytes: int, nstreams: int = 4, flags: int = 0):
+    s = load().fft_server_create(int(budget_bytes), int(nstreams), int(flags))
+    if not s:
+        raise GbfftError(fft_last_error(), "fft_server_create")
+    return s
+
+
+def fft_server_now(server) -> float:
+    return load().fft_server_now(server)
+
+
+def fft_server_submit(server, n, batch, sign, host_in_ptr, host_out_ptr, arrival=-1.0) -> int:
+    """Submit a dense row-major transform (lengths n, last fastest); returns the ticket."""
+    arr = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    t = ctypes.c_uint64(0)
+    rc = load().fft_server_submit(server, len(n), arr, int(batch), int(sign), ctypes.c_void_p(host_in_ptr),
+                                  ctypes.c_void_p(host_out_ptr), float(arrival), ctypes.byref(t))
+    if rc != FFT_OK:
+        raise GbfftError(rc, "fft_server_submit")
+    return t.value
+
+
+def fft_server_poll(server, ticket) -> int:
+    return load().fft_server_poll(server, int(ticket))
+
+
+def fft_server_wait(server, ticket, timeout_s=60.0) -> int:
+    return load().fft_server_wait(server, int(ticket), float(timeout_s))
+
+
+def fft_server_drain(server, timeout_s=600.0) -> int:
+    return load().fft_server_drain(server, float(timeout_s))
+
+
+def fft_server_stats(server) -> dict:
+    import json
+    return json.loads(_text(load().fft_server_stats, server))
+
+
+def fft_server_destroy(server) -> None:
+    if server:
+        load().fft_server_destroy(server)
 
 
 def fft_execute_1d_noalloc(n: int, batch: int, sign: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:

@@ -1,0 +1,137 @@
+"""Uneven batches in one persistent launch (fft_group_*): every transform of
+every plan matches the FP64 oracle (relative L2 <= 2e-6) and its own plan run
+alone; CUDA-graph replays and pointer changes keep results; a device wait that
+runs out reports FFT_ERR_DEVICE_TIMEOUT and leaves the context usable."""
+import numpy as np
+import pytest
+
+import fft_inputs
+from parity import TOL, per_transform_error, reference
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2602_23525_gb300 import gbfft  # noqa: E402
+
+EST = gbfft.FFT_ESTIMATE
+
+
+def uneven_problems(batch):
+    probs = []
+    for i, n in enumerate(fft_inputs.UNEVEN_SIZES):
+        if n in fft_inputs.UNEVEN_TRANSPOSED:
+            dims, how = fft_inputs.transposed_1d(n, batch)
+        else:
+            dims, how = fft_inputs.batched_1d(n, batch)
+        x = fft_inputs.gaussian_c64(n * batch, fft_inputs.seed_for(2, i))
+        probs.append((n, dims, how, x))
+    return probs
+
+
+def run_group(probs, sign, stream, flags=0, repeat=1):
+    plans = [gbfft.Plan(d, h, sign, EST) for _, d, h, _ in probs]
+    ins = [torch.from_numpy(x).cuda() for *_, x in probs]
+    outs = [torch.zeros_like(t) for t in ins]
+    g = gbfft.fft_group_create([p.handle for p in plans], flags)
+    try:
+        for _ in range(repeat):
+            gbfft.fft_group_execute(g, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], stream)
+        torch.cuda.synchronize()
+        status = gbfft.fft_group_status(g)
+        alone = []
+        for p, t in zip(plans, ins):
+            y = torch.zeros_like(t)
+            p.execute(t, y)
+            alone.append(y)
+        torch.cuda.synchronize()
+    finally:
+        gbfft.fft_group_destroy(g)
+    res = [o.cpu().numpy() for o in outs], [a.cpu().numpy() for a in alone], status
+    for p in plans:
+        p.destroy()
+    return res
+
+
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_uneven_group_matches_oracle_and_alone(sign):
+    probs = uneven_problems(8)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        outs, alone, status = run_group(probs, sign, s.cuda_stream, repeat=2)
+    assert status == gbfft.FFT_OK
+    for (n, dims, how, x), y, a in zip(probs, outs, alone):
+        ref = reference(dims, how, sign, x, algo="ct" if n > 4096 else "auto")
+        err = per_transform_error(y, ref, dims, how)
+        assert err.max() <= TOL, (n, err.max())
+        assert per_transform_error(y, a.astype(np.complex128), dims, how).max() <= TOL
+
+
+def test_group_on_legacy_stream_and_pointer_change():
+    probs = uneven_problems(4)[:4]
+    plans = [gbfft.Plan(d, h, -1, EST) for _, d, h, _ in probs]
+    ins = [torch.from_numpy(x).cuda() for *_, x in probs]
+    g = gbfft.fft_group_create([p.handle for p in plans])
+    s = torch.cuda.Stream()
+    results = []
+    for stream in (0, s.cuda_stream, s.cuda_stream):
+        outs = [torch.zeros_like(t) for t in ins]  # new pointers every time
+        gbfft.fft_group_execute(g, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], stream)
+        torch.cuda.synchronize()
+        results.append([o.cpu().numpy() for o in outs])
+    assert gbfft.fft_group_status(g) == gbfft.FFT_OK
+    gbfft.fft_group_destroy(g)
+    for r in results[1:]:
+        for a, b in zip(results[0], r):
+            assert np.array_equal(a, b)
+    for (n, dims, how, x), y in zip(probs, results[0]):
+        ref = reference(dims, how, -1, x)
+        assert per_transform_error(y, ref, dims, how).max() <= TOL
+    for p in plans:
+        p.destroy()
+
+
+def test_group_wait_timeout_is_reported_and_context_survives():
+    probs = uneven_problems(2)[:2]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        outs, alone, status = run_group(probs, -1, s.cuda_stream, flags=gbfft.FFT_GROUP_DEBUG_STALL)
+    assert status == gbfft.FFT_ERR_DEVICE_TIMEOUT
+    # the real items still completed, and the context still runs plans
+    for (n, dims, how, x), y in zip(probs, outs):
+        ref = reference(dims, how, -1, x)
+        assert per_transform_error(y, ref, dims, how).max() <= TOL
+    n = 4096
+    x = fft_inputs.uniform_c64(n * 4, 5)
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.zeros_like(xt)
+    p = gbfft.Plan([(n, 1, 1)], [(4, n, n)], -1, EST)
+    p.execute(xt, yt)
+    torch.cuda.synchronize()
+    ref = reference([(n, 1, 1)], [(4, n, n)], -1, x)
+    assert per_transform_error(yt.cpu().numpy(), ref, [(n, 1, 1)], [(4, n, n)]).max() <= TOL
+    p.destroy()
+
+
+def test_uneven_full_size_sampled():
+    """The full uneven workload (6 sizes x 512, mixed layouts) in one launch;
+    sampled transforms (first, middle, last of each size) against the oracle."""
+    batch = fft_inputs.UNEVEN_BATCH
+    probs = uneven_problems(batch)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        outs, alone, status = run_group(probs, -1, s.cuda_stream)
+    assert status == gbfft.FFT_OK
+    for (n, dims, how, x), y in zip(probs, outs):
+        for v in (0, batch // 2, batch - 1):
+            if n in fft_inputs.UNEVEN_TRANSPOSED:
+                xi = x[v::batch]        # column v in, row v out
+                yi = y[v * n:(v + 1) * n]
+            else:
+                xi = x[v * n:(v + 1) * n]
+                yi = y[v * n:(v + 1) * n]
+            ref = reference([(n, 1, 1)], [], -1, xi, algo="ct" if n > 4096 else "auto")
+            err = np.linalg.norm(yi.astype(np.complex128) - ref) / np.linalg.norm(ref)
+            assert err <= TOL, (n, v, err)
