@@ -390,6 +390,59 @@ def run_uneven(args):
     return res
 
 
+def run_precision(args):
+    """The tensor-core precision forms on the two precision workloads: batch 65536
+    of n = 4096, and 256^3.  Each form (FP32 path, FP16, BF16, FP16 split, BF16
+    split) is timed and its error against the FP64 oracle stated (sampled
+    transforms for the batch, the whole cube for 256^3)."""
+    import torch
+
+    import oracle
+    from paper_2602_23525_gb300 import gbfft
+    forms = {"fp32": 0, "tc-fp16": gbfft.FFT_PREC_TC_FP16, "tc-bf16": gbfft.FFT_PREC_TC_BF16,
+             "tc-fp16-split": gbfft.FFT_PREC_TC_FP16 | gbfft.FFT_PREC_SPLIT,
+             "tc-bf16-split": gbfft.FFT_PREC_TC_BF16 | gbfft.FFT_PREC_SPLIT}
+    cases = [("batch 65536 x n=4096", [(4096, 1, 1)], [(65536, 4096, 4096)], 4096, 65536),
+             ("256^3", [(256, 65536, 65536), (256, 256, 256), (256, 1, 1)], [], 256 ** 3, 1)]
+    out = {"metric": METRIC, "unit": "GFLOP/s", "workload": "precision forms", "cases": []}
+    for label, dims, how, npts, count in cases:
+        total = npts * count
+        x_np = fft_inputs.uniform_c64(total, fft_inputs.seed_for(3, 0))
+        x = torch.from_numpy(x_np).cuda()
+        y = torch.empty_like(x)
+        if count > 1:
+            idx = [0, count // 3, count - 1]
+            refs = {v: oracle.dft(x_np[v * npts:(v + 1) * npts], [(npts, 1, 1)], [], -1) for v in idx}
+        else:
+            refs = {0: oracle.dft(x_np, dims, [], -1, algo="ct")}
+        res = {"case": label, "forms": {}}
+        for name, fl in forms.items():
+            p = gbfft.Plan(dims, how, -1, fl | gbfft.FFT_ESTIMATE)
+            s = torch.cuda.current_stream().cuda_stream
+            for _ in range(args.warmup):
+                gbfft.fft_execute(p.handle, x.data_ptr(), y.data_ptr(), s)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(args.steps):
+                gbfft.fft_execute(p.handle, x.data_ptr(), y.data_ptr(), s)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / args.steps
+            yh = y.cpu().numpy()
+            errs = []
+            for v, ref in refs.items():
+                yy = yh[v * npts:(v + 1) * npts].astype(np.complex128)
+                errs.append(float(np.linalg.norm(yy - ref) / np.linalg.norm(ref)))
+            res["forms"][name] = {"ms": round(ms, 4), "gflops": round(flops_of(npts, count) / (ms * 1e-3) / 1e9, 1),
+                                  "gbs_algorithmic": round(16.0 * total / (ms * 1e-3) / 1e9, 1),
+                                  "max_rel_l2_vs_fp64_oracle": max(errs),
+                                  "passes": [ln.strip().split(" n=")[0] for ln in p.info.splitlines()
+                                             if ln.strip().startswith("pass")]}
+            p.destroy()
+        out["cases"].append(res)
+    return out
+
+
 def run_serving(args):
     """The serving workload: requests of mixed shapes (rank 1-3), batches and signs
     with Poisson arrivals, admitted by a 40 GB work-buffer budget.  The arrival
@@ -437,7 +490,7 @@ def run_serving(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "uneven", "serving"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "uneven", "serving", "precision"],
                     help="sweep: the benchmark step; uneven / serving: extra workloads (their own line)")
     ap.add_argument("--requests", type=int, default=100000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: 0.7 x capacity)")
@@ -455,9 +508,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     args.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload in ("uneven", "serving"):
+    if args.workload in ("uneven", "serving", "precision"):
         if rank == 0:
-            fn = run_uneven if args.workload == "uneven" else run_serving
+            fn = {"uneven": run_uneven, "serving": run_serving, "precision": run_precision}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":

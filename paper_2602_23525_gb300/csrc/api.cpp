@@ -50,10 +50,6 @@ fft_plan fft_plan_dft(int rank, const fft_iodim* dims, int howmany_rank, const f
     set_err(rc);
     return nullptr;
   }
-  if (flags & (FFT_PREC_TC_FP16 | FFT_PREC_TC_BF16 | FFT_PREC_SPLIT)) {
-    set_err(FFT_ERR_UNSUPPORTED);
-    return nullptr;
-  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();

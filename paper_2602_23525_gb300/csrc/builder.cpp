@@ -59,6 +59,7 @@ struct Builder {
   std::map<int64_t, const float2*> roots_cache;
   std::map<int64_t, std::pair<const float2*, const float2*>> split_cache;
   std::map<std::string, std::string> forced;  // choices imposed while timing a candidate
+  int prec = 0;  // 0 FP32; tensor-core radix-16 stages: 1 FP16, 2 BF16, 3 FP16 split, 4 BF16 split
   int err = FFT_OK;
 
   Builder(PlanData* p, bool dev, bool meas, bool wonly) : P(p), device(dev), measure(meas), wisdom_only(wonly) {}
@@ -324,12 +325,12 @@ struct Builder {
   // the tile dimension (ROWS / COLS), and every offset a bulk copy starts at
   // is even (16 bytes).
   struct P2Choice {
-    int logn = -1, load = -1, store = -1, T = 1;
+    int logn = -1, load = -1, store = -1, T = 1, prec = 0;
     Dim v0{1, 0, 0};
     std::vector<Dim> rest;
   };
 
-  static bool p2_choose(const Dim& d, const std::vector<Dim>& Vin, bool posttw, P2Choice* c) {
+  static bool p2_choose(const Dim& d, const std::vector<Dim>& Vin, bool posttw, P2Choice* c, int prec = 0) {
     const int e = log2_exact(d.n);
     if (e < 0 || Vin.size() > 3) return false;
     const std::vector<Dim> V = order_for_pass(Vin);
@@ -349,6 +350,13 @@ struct Builder {
     }
     if (ch.load < 0 || ch.store < 0 || !gb_p2_supported(e, ch.load, ch.store, posttw ? 1 : 0)) return false;
     ch.T = gb_p2_tile(e, ch.load, ch.store);
+    ch.prec = 0;
+    if (prec && gb_tc_supported(e, ch.load, ch.store, posttw ? 1 : 0)) {
+      ch.prec = prec;
+      ch.T = gb_tc_tile(e, ch.load, ch.store);
+      if ((ch.load == GB_P2_LOAD_ROWS || ch.store == GB_P2_STORE_COLS) && v0.n % ch.T != 0) ch.prec = 0;
+      if (ch.prec == 0) ch.T = gb_p2_tile(e, ch.load, ch.store);
+    }
     if (ch.load == GB_P2_LOAD_CONTIG && ch.store == GB_P2_STORE_CONTIG && gb_p2_small(e)) {
       // small transforms: adjacent on both sides, one vector loop
       if (!ch.rest.empty() || (v0.n > 1 && (v0.is != d.n || v0.os != d.n))) return false;
@@ -364,11 +372,12 @@ struct Builder {
 
   void emit_p2(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t posttwN, int depth) {
     P2Choice c;
-    if (!p2_choose(d, V, posttwN > 0, &c)) {
+    if (!p2_choose(d, V, posttwN > 0, &c, prec)) {
       err = FFT_ERR_WISDOM;
       return;
     }
     GbP2 k{};
+    k.prec = c.prec;
     k.logn = c.logn;
     k.load = c.load;
     k.store = c.store;
@@ -423,7 +432,8 @@ struct Builder {
     static const char* ln[] = {"contig", "rows"};
     static const char* sn[] = {"contig", "cols"};
     std::ostringstream o;
-    o << "pass p2-tma n=" << d.n << " load=" << ln[c.load] << " store=" << sn[c.store] << " T=" << c.T
+    static const char* pn[] = {"p2-tma", "tc-fp16", "tc-bf16", "tc-fp16-split", "tc-bf16-split"};
+    o << "pass " << pn[c.prec] << " n=" << d.n << " load=" << ln[c.load] << " store=" << sn[c.store] << " T=" << c.T
       << " is=" << d.is << " os=" << d.os << " tile=" << dims_str({c.v0}) << " rest=" << dims_str(c.rest)
       << (k.posttw ? " post-twiddle w_" + std::to_string(posttwN) + "^(v0*k)" : std::string()) << (conj ? " conj" : "")
       << " (fallback: " << desc << ")";
@@ -592,9 +602,10 @@ struct Builder {
 
   // ---------------------------------------------------------------- planner
 
-  static std::string key_rank1(const Dim& d, const std::vector<Dim>& V, bool inplace) {
+  std::string key_rank1(const Dim& d, const std::vector<Dim>& V, bool inplace) const {
     std::ostringstream o;
     o << "r1 n=" << d.n << " is=" << d.is << " os=" << d.os << " v=" << dims_str(V) << " ip=" << (inplace ? 1 : 0);
+    if (prec) o << " tc=" << prec;
     return o.str();
   }
 
@@ -608,7 +619,10 @@ struct Builder {
       has_v = true;
     }
     P2Choice pc;
-    if (p2_choose(d, V, false, &pc)) c.push_back("p2");
+    if (p2_choose(d, V, false, &pc, prec)) {
+      c.push_back("p2");
+      if (pc.prec) return c;  // the requested tensor-core precision decides the pass
+    }
     const int lg = log2_exact(n);
     if (lg >= 14 && smooth_codelet(n)) {
       // power of two beyond the one-CTA kernels: TMA passes of a split first
@@ -829,7 +843,7 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
         GbP2 k = s.p2;
         k.in = bufs[s.src];
         k.out = bufs[s.dst];
-        e = gb_launch_p2(k, st);
+        e = k.prec ? gb_launch_tc(k, st) : gb_launch_p2(k, st);
       }
       else
         e = gb_launch_pass(s.pass, s.dpass, bufs[s.src], bufs[s.dst], s.threads, s.smem, s.grid, st);
@@ -905,6 +919,7 @@ double Builder::time_choice(const Dim& d, const std::vector<Dim>& Vin, bool inpl
   }
   cudaMemset(tmp.d_status, 0, sizeof(int));
   Builder b(&tmp, true, true, false);
+  b.prec = prec;
   b.forced = forced;
   b.forced[key] = choice;
   b.forced[key_rank1(d, canon_vec(V), inplace)] = choice;
@@ -977,6 +992,8 @@ int build_plan(const Problem& P, bool device, PlanData* out) {
   }
   const bool measure = device && !(P.flags & FFT_ESTIMATE);
   Builder b(out, device, measure, (P.flags & FFT_WISDOM_ONLY) != 0);
+  if (P.flags & (FFT_PREC_TC_FP16 | FFT_PREC_TC_BF16))
+    b.prec = ((P.flags & FFT_PREC_TC_FP16) ? 1 : 2) + ((P.flags & FFT_PREC_SPLIT) ? 2 : 0);
   const int conj = P.sign > 0 ? 1 : 0;
   b.solve(P.N, P.V, BUF_IN, out->inplace ? BUF_IN : BUF_OUT, conj, 1);
   if (!b.err && device && cudaStreamSynchronize(0) != cudaSuccess) b.err = FFT_ERR_CUDA;

@@ -20,6 +20,7 @@ enum { GB_P2_LOAD_CONTIG = 0, GB_P2_LOAD_ROWS = 1 };     // is == 1  |  vis0 == 
 enum { GB_P2_STORE_CONTIG = 0, GB_P2_STORE_COLS = 1 };   // os == 1  |  vos0 == 1
 struct GbP2 {
   int logn, load, store, posttw;
+  int prec;           // 0 FP32; tensor-core radix-16 stages: 1 FP16, 2 BF16, 3 FP16 split, 4 BF16 split
   const float2* in;   // set at execute time
   float2* out;
   int64_t V0, is, os, vis0, vos0;
@@ -38,6 +39,10 @@ int gb_p2_twiddle_elems(int logn);               // float2 entries of the stage 
 int gb_p2_stage(int logn, int s, int* L, int* R, int* offset);
 int gb_p2_last_L(int logn);
 cudaError_t gb_launch_p2(const GbP2& k, cudaStream_t st);
+// tensor-core variants (tc.cu): 2^12 contiguous tiles, 2^8 contiguous or column tiles
+int gb_tc_supported(int logn, int load, int store, int posttw);
+int gb_tc_tile(int logn, int load, int store);
+cudaError_t gb_launch_tc(const GbP2& k, cudaStream_t st);
 
 // Bluestein helper kernels for convolution lengths beyond one CTA (bluestein.cu).
 struct GbBlueIO {

@@ -70,6 +70,8 @@ int canonicalize(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, i
   if ((rank > 0 && !dims) || (hr > 0 && !hd)) return FFT_ERR_INVALID_ARG;
   if (sign != -1 && sign != 1) return FFT_ERR_INVALID_ARG;
   if (flags & ~kKnownFlags) return FFT_ERR_INVALID_ARG;
+  if ((flags & FFT_PREC_TC_FP16) && (flags & FFT_PREC_TC_BF16)) return FFT_ERR_INVALID_ARG;
+  if ((flags & FFT_PREC_SPLIT) && !(flags & (FFT_PREC_TC_FP16 | FFT_PREC_TC_BF16))) return FFT_ERR_INVALID_ARG;
   if (rank > 3 || hr > 3) return FFT_ERR_UNSUPPORTED;
   P = Problem();
   P.sign = sign;
