@@ -51,4 +51,16 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
+// tiled tensor copy of one box through a tensor map (a __grid_constant__
+// kernel parameter); coordinates innermost first, x * element size a
+// multiple of 16 bytes
+__device__ __forceinline__ void tensor_copy_4d(uint32_t dst, const void* tmap, int x, int y, int z, int w,
+                                               uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+      : "memory");
+}
+
 }  // namespace

@@ -21,8 +21,11 @@
 //                transform.
 //   LOAD_ROWS:   the tile is T adjacent columns of a row-major matrix whose
 //                columns are the transforms (unit stride along the tile
-//                dimension): one copy of T elements per row -- the strided
-//                first pass of a four-step plan (sec. 3.3, radix-sqrt(n)).
+//                dimension) -- the strided first pass of a four-step plan
+//                (sec. 3.3, radix-sqrt(n)).  The tile arrives as tensor-map
+//                boxes of T columns x up to 256 rows (cp.async.bulk.tensor,
+//                one instruction per box); where no tensor map can describe
+//                the layout, as one bulk copy of T elements per row.
 // and two store shapes: STORE_CONTIG (unit element stride, lanes along the
 // transform) and STORE_COLS (unit stride along the tile dimension, lanes
 // across the T transforms, so T adjacent outputs form one segment).
@@ -30,8 +33,14 @@
 // w_N^{l2 k1} of eq. (2) (l2 = column, k1 = output index).
 // Every mbarrier wait is bounded by %globaltimer; on timeout the CTA records
 // FFT_ERR_DEVICE_TIMEOUT in the status word and returns.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
+
+#include <cstring>
+#include <mutex>
+#include <utility>
 
 #include "codelets.cuh"
 #include "gb_kernels.h"
@@ -39,6 +48,14 @@
 
 namespace {
 
+
+// Tensor map of a LOAD_ROWS input: dims (column, row, two vector loops),
+// the vector loops ordered by stride; swap = 1 when that order is (nb2, nb1).
+struct GbRowsMap {
+  CUtensorMap map;
+  int use;
+  int swap;
+};
 
 template <int LOGN>
 struct P2 {
@@ -191,7 +208,8 @@ __device__ __forceinline__ void later_stages(float2* v, float2* xrow_j, float2* 
 // Stage 0 uses the mapping that reads the landed tile without bank conflicts,
 // the last stage the one that makes the global stores coalesce.
 template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW>
-__global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB) gb_p2_kernel(const __grid_constant__ GbP2 k) {
+__global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
+    gb_p2_kernel(const __grid_constant__ GbP2 k, const __grid_constant__ GbRowsMap rm) {
   using C = P2<LOGN>;
   constexpr int TILE = T * C::N;  // elements per tile buffer
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -249,8 +267,19 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB) gb_p2_kernel(const _
       // element e of column t lands at dst[e * T + t]
       if (lane == 0) expect_tx(bar, (uint32_t)(C::N * T * 8));
       __syncwarp();
-      for (int e = lane; e < C::N; e += 32)
-        bulk_copy(smem_addr(dst + e * T), k.in + ib + (int64_t)e * k.is, (uint32_t)(T * 8), bar);
+      if (rm.use) {
+        if (lane == 0) {
+          const int64_t r = tile / cblocks;
+          const int b1 = (int)(r % k.nb1), b2 = (int)(r / k.nb1);
+          constexpr int BOXR = C::N < 256 ? C::N : 256;
+#pragma unroll
+          for (int r0 = 0; r0 < C::N; r0 += BOXR)
+            tensor_copy_4d(smem_addr(dst + r0 * T), &rm.map, (int)c0, r0, rm.swap ? b2 : b1, rm.swap ? b1 : b2, bar);
+        }
+      } else {
+        for (int e = lane; e < C::N; e += 32)
+          bulk_copy(smem_addr(dst + e * T), k.in + ib + (int64_t)e * k.is, (uint32_t)(T * 8), bar);
+      }
     }
   };
 
@@ -303,9 +332,65 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB) gb_p2_kernel(const _
   }
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map for the LOAD_ROWS tiles of k: 8-byte elements, dims (V0 columns,
+// n rows, the two vector loops by increasing stride), box (T, min(n, 256), 1, 1).
+// Leaves rm->use = 0 (per-row bulk copies) when the layout has no such map:
+// an unaligned base, a stride that is not a multiple of 16 bytes or that
+// decreases along the dims, or an encoder error.
+void make_rows_map(const GbP2& k, int T, GbRowsMap* rm) {
+  memset(rm, 0, sizeof(*rm));
+  if (k.load != GB_P2_LOAD_ROWS || k.vis0 != 1) return;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(k.in) & 15)) return;
+  const int64_t n = int64_t(1) << k.logn;
+  struct D {
+    int64_t n, s;
+  } a{k.nb1, k.vis1 * 8}, b{k.nb2, k.vis2 * 8};
+  auto first = [](const D& x, const D& y) { return (x.n > 1) != (y.n > 1) ? x.n > 1 : x.s <= y.s; };
+  int swap = 0;
+  if (!first(a, b)) {
+    std::swap(a, b);
+    swap = 1;
+  }
+  cuuint64_t dim[4] = {(cuuint64_t)k.V0, (cuuint64_t)n, (cuuint64_t)a.n, (cuuint64_t)b.n};
+  cuuint64_t str[3] = {(cuuint64_t)(k.is * 8), (cuuint64_t)a.s, (cuuint64_t)b.s};
+  if (a.n == 1) str[1] = str[0] * n;  // extent-1 dims: any valid stride
+  if (b.n == 1) str[2] = str[1] * a.n;
+  if (k.is <= 0 || a.s <= 0 || b.s <= 0) return;
+  for (int i = 0; i < 3; ++i)
+    if ((str[i] & 15) || str[i] >= (cuuint64_t(1) << 40)) return;
+  if (str[0] < (cuuint64_t)(k.V0 * 8) || str[1] < str[0] || str[2] < str[1]) return;
+  for (int i = 0; i < 4; ++i)
+    if (dim[i] < 1 || dim[i] > (cuuint64_t(1) << 32)) return;
+  cuuint32_t box[4] = {(cuuint32_t)T, (cuuint32_t)(n < 256 ? n : 256), 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  if (enc(&rm->map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<float2*>(k.in), dim, str, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return;
+  rm->use = 1;
+  rm->swap = swap;
+}
+
 template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW>
 cudaError_t launch(const GbP2& k, cudaStream_t st) {
   using C = P2<LOGN>;
+  static_assert(LOAD != GB_P2_LOAD_ROWS || (T % 2 == 0), "tensor-map boxes need 16-byte rows");
   const size_t smem = 128 + sizeof(float2) * ((size_t)NBUF * T * C::N + (C::NST > 1 ? (size_t)T * C::PITCH : 0));
   auto fn = gb_p2_kernel<LOGN, T, NBUF, MINB, LOAD, STORE, POSTTW>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -321,7 +406,9 @@ cudaError_t launch(const GbP2& k, cudaStream_t st) {
   if (k.grid > 0) grid = k.grid;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) return cudaSuccess;
-  fn<<<(unsigned)grid, T * C::TPT, smem, st>>>(k);
+  GbRowsMap rm;
+  make_rows_map(k, T, &rm);
+  fn<<<(unsigned)grid, T * C::TPT, smem, st>>>(k, rm);
   return cudaGetLastError();
 }
 
@@ -439,11 +526,13 @@ cudaError_t launch_small(const GbP2& k, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// transforms per CTA tile, by size and tile shape (tiles of 32-64 KB)
+// transforms per CTA tile, by size and tile shape (tiles of 32-64 KB); column
+// tiles are at least 16 columns (128-byte row segments) and 4096 points below
+// n = 256, so that n = 64 / 128 move 512 / 256-byte row segments
 constexpr int tile_T(int logn, int load, int store) {
   return (load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG)
              ? (logn <= 12 ? (1 << (12 - logn)) : 1)
-             : (logn <= 9 ? 16 : (logn == 10 ? 8 : (logn == 11 ? 4 : 2)));
+             : (logn <= 7 ? (1 << (12 - logn)) : logn <= 9 ? 16 : (logn == 10 ? 8 : (logn == 11 ? 4 : 2)));
 }
 
 constexpr int min_blocks(int logn, int load, int store) {

@@ -244,7 +244,7 @@ def test_p2_strided_tile_shapes():
     """Column tiles (rows of adjacent columns in, rows or columns out) of the TMA
     pass kernels, with two extra vector loops and ragged column counts rejected
     back to the generic pass."""
-    for n, cols, b in [(64, 48, 3), (512, 32, 2), (1024, 16, 2), (4096, 4, 2)]:
+    for n, cols, b in [(64, 192, 3), (128, 96, 2), (512, 32, 2), (1024, 16, 2), (4096, 4, 2)]:
         x = u(n * cols * b, 50 + n)
         # columns of a row-major n x cols matrix, b matrices
         err, info = check([(n, cols, cols)], [(cols, 1, 1), (b, n * cols, n * cols)], +1, x, flags=EST)
@@ -257,6 +257,25 @@ def test_p2_strided_tile_shapes():
     x = u(1024 * 20, 61)
     err, info = check([(1024, 1, 20)], [(20, 1024, 1)], -1, x, flags=EST)
     assert "p2-tma" not in info and "pass stockham" in info
+
+
+def test_p2_rows_tensor_map_layouts():
+    """Column tiles loaded through a tensor map: padded row pitch and two
+    unmergeable vector loops in either stride order; and a layout whose vector
+    stride is below the row stride (no tensor map: one bulk copy per row)."""
+    n, cols, b1, b2 = 256, 32, 3, 2
+    pitch = cols + 8
+    s2 = n * pitch
+    s1 = b2 * s2 + 64
+    x = u(b1 * s1, 81)
+    for how in ([(cols, 1, 1), (b1, s1, n * cols * b2), (b2, s2, n * cols)],
+                [(cols, 1, 1), (b2, s2, n * cols), (b1, s1, n * cols * b2)]):
+        err, info = check([(n, pitch, cols)], how, -1, x, flags=EST)
+        assert "load=rows" in info
+    B = 4
+    x = u(n * B * (cols + 2), 82)
+    err, info = check([(n, B * (cols + 2), cols)], [(cols, 1, 1), (B, cols + 2, n * cols)], 1, x, flags=EST)
+    assert "load=rows" in info
 
 
 @pytest.mark.parametrize("e", [4, 5, 6, 7])
