@@ -165,6 +165,14 @@ extern "C" int fft_import_wisdom(const char* text) {
       if (atoll(val.c_str() + 6) < 2) return set_err(FFT_ERR_WISDOM);
     } else if (val.rfind("blue:", 0) == 0) {
       if (atoll(val.c_str() + 5) < 3) return set_err(FFT_ERR_WISDOM);
+    } else if (val.rfind("cluster:", 0) == 0) {
+      int l1 = 0, l2 = 0, cs = 0, nb = 0, cfg[16][4];
+      if (sscanf(val.c_str(), "cluster:%d.%d.%d.%d", &l1, &l2, &cs, &nb) != 4) return set_err(FFT_ERR_WISDOM);
+      const int nc = gb_cluster_configs(l1 + l2, cfg, 16);
+      bool known = false;
+      for (int i = 0; i < nc; ++i)
+        known |= cfg[i][0] == l1 && cfg[i][1] == l2 && cfg[i][2] == cs && cfg[i][3] == nb;
+      if (!known) return set_err(FFT_ERR_WISDOM);
     } else {
       return set_err(FFT_ERR_WISDOM);
     }

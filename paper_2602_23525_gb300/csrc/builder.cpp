@@ -440,6 +440,88 @@ struct Builder {
     line(depth, o.str());
   }
 
+  // One-pass cluster kernel (cluster.cu) for contiguous transforms of
+  // 2^13..2^17 points, at most one vector loop.
+  static bool cluster_ok(const Dim& d, const std::vector<Dim>& V) {
+    const int e = log2_exact(d.n);
+    if (e < 13 || e > 17 || d.is != 1 || d.os != 1 || V.size() > 1) return false;
+    if (!V.empty() && (V[0].is <= 0 || V[0].os <= 0)) return false;
+    return true;
+  }
+
+  bool cluster_parse(const std::string& c, int* l1, int* l2, int* cs, int* nb) {
+    return sscanf(c.c_str(), "cluster:%d.%d.%d.%d", l1, l2, cs, nb) == 4;
+  }
+
+  void emit_cluster(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int l1, int l2, int cs,
+                    int nb, int depth) {
+    const int e = log2_exact(d.n);
+    int cfg[16][4];
+    const int nc = gb_cluster_configs(e, cfg, 16);
+    bool known = false;
+    for (int i = 0; i < nc; ++i) known |= cfg[i][0] == l1 && cfg[i][1] == l2 && cfg[i][2] == cs && cfg[i][3] == nb;
+    if (!known || !cluster_ok(d, V)) {
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    GbCluster k{};
+    k.logn1 = l1;
+    k.logn2 = l2;
+    k.csize = cs;
+    k.nbuf = nb;
+    k.count = V.empty() ? 1 : V[0].n;
+    k.vis = V.empty() ? d.n : V[0].is;
+    k.vos = V.empty() ? d.n : V[0].os;
+    k.conj = conj;
+    k.status = P->d_status;
+    const int64_t n1 = int64_t(1) << l1, n2 = int64_t(1) << l2;
+    float2* t1 = (float2*)dalloc(sizeof(float2) * (size_t)std::max(16, gb_p2_twiddle_elems(l1)));
+    float2* t2 = (float2*)dalloc(sizeof(float2) * (size_t)std::max(16, gb_p2_twiddle_elems(l2)));
+    for (int st = 1; t1 && t2 && !err; ++st) {
+      int L, R, off, any = 0;
+      if (gb_p2_stage(l1, st, &L, &R, &off)) {
+        any = 1;
+        if (gb_make_stage_twiddles(t1 + off, n1, L, R, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+      }
+      if (gb_p2_stage(l2, st, &L, &R, &off)) {
+        any = 1;
+        if (gb_make_stage_twiddles(t2 + off, n2, L, R, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+      }
+      if (!any) break;
+    }
+    const int64_t Ll = gb_p2_last_L(l1);
+    float2* A = (float2*)dalloc(sizeof(float2) * (size_t)(n2 * Ll));
+    float2* B = (float2*)dalloc(sizeof(float2) * (size_t)(n2 * 4));
+    if (A && B && gb_make_posttw(A, B, d.n, n2, Ll, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+    k.tw1 = t1;
+    k.tw2 = t2;
+    k.ptwA = A;
+    k.ptwB = B;
+    Step s;
+    std::string desc = "none";
+    std::vector<int> rad = default_radices(d.n);
+    if (single_pass_ok(d.n, rad)) {
+      // a one-CTA pass over the same sub-problem (the persistent group executor runs that)
+      Dim v0 = V.empty() ? Dim{1, 0, 0} : V[0];
+      const int saved = err;
+      if (!make_single(d, V, src, dst, conj, estimate_cfg(d, v0, !V.empty(), rad), nullptr, &s, &desc)) {
+        err = saved;  // no fallback: the plan still runs, only not inside a group
+        s = Step();
+        desc = "none";
+      }
+    }
+    s.src = src;
+    s.dst = dst;
+    s.kind = STEP_CLUSTER;
+    s.cl = k;
+    P->steps.push_back(s);
+    std::ostringstream o;
+    o << "pass cluster n=" << d.n << " = " << n1 << " x " << n2 << " C=" << cs << " buffers=" << nb << " (eq. 2 over " << cs
+      << " CTAs, distributed shared memory exchange) T=" << n2 / cs << " R=" << n1 / cs << " count=" << k.count
+      << " vis=" << k.vis << " vos=" << k.vos << (conj ? " conj" : "") << " (one-CTA fallback: " << desc << ")";
+    line(depth, o.str());
+  }
+
   void emit_fourstep(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t n1,
                      int depth) {
     const int64_t n = d.n, n2 = n / n1;
@@ -624,6 +706,19 @@ struct Builder {
       if (pc.prec) return c;  // the requested tensor-core precision decides the pass
     }
     const int lg = log2_exact(n);
+    if (!prec && cluster_ok(d, V)) {
+      int cfg[16][4];
+      const int nc = gb_cluster_configs(lg, cfg, 16);
+      for (int i = 0; i < nc; ++i) {
+        if (device && gb_cluster_max_active(cfg[i][0], cfg[i][1], cfg[i][2], cfg[i][3]) < 1) {
+          cudaGetLastError();
+          continue;
+        }
+        c.push_back("cluster:" + std::to_string(cfg[i][0]) + "." + std::to_string(cfg[i][1]) + "." +
+                    std::to_string(cfg[i][2]) + "." + std::to_string(cfg[i][3]));
+        if (!measure) break;
+      }
+    }
     if (lg >= 14 && smooth_codelet(n)) {
       // power of two beyond the one-CTA kernels: TMA passes of a split first
       const int64_t a = estimate_split(n);
@@ -763,6 +858,13 @@ struct Builder {
         return;
       }
       emit_single(d, order_for_pass(V), src, dst, conj, cfg, nullptr, depth);
+    } else if (choice.rfind("cluster:", 0) == 0) {
+      int l1, l2, cs, nb;
+      if (!cluster_parse(choice, &l1, &l2, &cs, &nb)) {
+        err = FFT_ERR_WISDOM;
+        return;
+      }
+      emit_cluster(d, V, src, dst, conj, l1, l2, cs, nb, depth);
     } else if (choice.rfind("split:", 0) == 0) {
       const int64_t n1 = atoll(choice.c_str() + 6);
       if (n1 < 2 || d.n % n1 != 0) {
@@ -847,6 +949,13 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
       }
       else
         e = gb_launch_pass(s.pass, s.dpass, bufs[s.src], bufs[s.dst], s.threads, s.smem, s.grid, st);
+      break;
+    }
+    case STEP_CLUSTER: {
+      GbCluster k = s.cl;
+      k.in = bufs[s.src];
+      k.out = bufs[s.dst];
+      e = gb_launch_cluster(k, st);
       break;
     }
     case STEP_COPY: {

@@ -33,6 +33,9 @@ struct GbP2 {
   int64_t grid;        // <= 0: persistent grid sized by occupancy
 };
 int gb_p2_supported(int logn, int load, int store, int posttw);
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
+// query, so the library needs no link-time libcuda); nullptr if unavailable
+void* gb_tensor_map_encoder(void);
 int gb_p2_tile(int logn, int load, int store);   // transforms per CTA tile
 int gb_p2_small(int logn);                       // 1: n = 2^logn uses the small-transform kernel
 int gb_p2_twiddle_elems(int logn);               // float2 entries of the stage tables
@@ -43,6 +46,33 @@ cudaError_t gb_launch_p2(const GbP2& k, cudaStream_t st);
 int gb_tc_supported(int logn, int load, int store, int posttw);
 int gb_tc_tile(int logn, int load, int store);
 cudaError_t gb_launch_tc(const GbP2& k, cudaStream_t st);
+
+// Single-pass transforms of n = 2^13 .. 2^17 spread over a thread-block
+// cluster (cluster.cu): n = n1 x n2 (eq. (2)); CTA s of the cluster computes
+// the n1-point DFTs of columns [s n2/C, (s+1) n2/C) with the twiddles
+// w_n^{l2 k1}, the CTAs exchange through distributed shared memory, and CTA r
+// computes the n2-point DFTs of rows [r n1/C, (r+1) n1/C).  Contiguous
+// transforms (unit stride) in a batch (count, vis, vos).
+struct GbCluster {
+  int logn1, logn2, csize;  // n1 = 2^logn1, n2 = 2^logn2, CTAs per cluster
+  int nbuf;                 // landing buffers per CTA (1 or 2)
+  const float2* in;         // set at execute time
+  float2* out;
+  int64_t count, vis, vos;
+  int conj;
+  const float2* tw1;   // stage tables of n1 (gb_make_stage_twiddles)
+  const float2* tw2;   // stage tables of n2
+  const float2* ptwA;  // w_n^{l2 k1}: A[l2*L + j], B[l2*4 + i] (gb_make_posttw, ncols = n2, L = last L of n1)
+  const float2* ptwB;
+  int* status;
+  int64_t clusters;    // <= 0: as many as are co-resident
+};
+// the (logn1, logn2, csize, nbuf) configurations of n = 2^logn, preferred
+// first; returns the count
+int gb_cluster_configs(int logn, int (*cfg)[4], int max_cfg);
+// co-resident clusters of a configuration on the current device (0: cannot launch)
+int gb_cluster_max_active(int logn1, int logn2, int csize, int nbuf);
+cudaError_t gb_launch_cluster(const GbCluster& k, cudaStream_t st);
 
 // Bluestein helper kernels for convolution lengths beyond one CTA (bluestein.cu).
 struct GbBlueIO {

@@ -35,7 +35,15 @@ struct PassCfg {
   bool parse(const std::string& s);
 };
 
-enum StepKind { STEP_PASS = 0, STEP_COPY = 1, STEP_BLUE_PRE = 2, STEP_BLUE_MUL = 3, STEP_BLUE_POST = 4, STEP_POW2 = 5 };
+enum StepKind {
+  STEP_PASS = 0,
+  STEP_COPY = 1,
+  STEP_BLUE_PRE = 2,
+  STEP_BLUE_MUL = 3,
+  STEP_BLUE_POST = 4,
+  STEP_POW2 = 5,
+  STEP_CLUSTER = 6
+};
 
 // Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.
 enum { BUF_IN = 0, BUF_OUT = 1, BUF_SCRATCH0 = 2 };
@@ -46,6 +54,7 @@ struct Step {
   const GbPass* dpass = nullptr;  // device copy of pass (what the kernel reads)
   GbP2 p2{};                      // STEP_POW2; pass/dpass hold the generic fallback
                                   // used when the input pointer is not 16-byte aligned
+  GbCluster cl{};                 // STEP_CLUSTER; pass/dpass hold a one-CTA fallback where one exists
   GbCopy copy{};
   GbBlueIO blue{};
   int src = BUF_IN, dst = BUF_OUT;

@@ -63,4 +63,12 @@ __device__ __forceinline__ void tensor_copy_4d(uint32_t dst, const void* tmap, i
       : "memory");
 }
 
+__device__ __forceinline__ void tensor_copy_3d(uint32_t dst, const void* tmap, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
 }  // namespace

@@ -116,6 +116,7 @@ extern "C" fft_group fft_group_create(int nplans, const fft_plan* plans, unsigne
       q.seg.dst = g->slot_base.back() + st.dst;
       switch (st.kind) {
         case STEP_PASS:
+        case STEP_CLUSTER:  // a cluster pass contributes its one-CTA fallback, where it has one
         case STEP_POW2: {  // a power-of-two pass contributes its generic fallback descriptor
           q.seg.kind = GB_SEG_PASS;
           q.seg.pass = st.dpass;

@@ -42,8 +42,8 @@
 #include <mutex>
 #include <utility>
 
-#include "codelets.cuh"
 #include "gb_kernels.h"
+#include "gb_p2_stages.cuh"
 #include "gb_tma.cuh"
 
 namespace {
@@ -56,151 +56,6 @@ struct GbRowsMap {
   int use;
   int swap;
 };
-
-template <int LOGN>
-struct P2 {
-  static constexpr int N = 1 << LOGN;
-  static constexpr int REM = LOGN % 4;
-  static constexpr int R0 = REM ? (1 << REM) : 16;
-  static constexpr int NST = LOGN / 4 + (REM ? 1 : 0);
-  static constexpr int TPT = N / 16;
-  static constexpr int PITCH = ((N + (N - 1) / 32 + 1) | 1);
-  __host__ __device__ static constexpr int radix(int s) { return s == 0 ? R0 : 16; }
-  __host__ __device__ static constexpr int L(int s) { return s == 0 ? 1 : R0 << (4 * (s - 1)); }
-  // stage s >= 1 table: [k][4] = (w, w^2, w^4, w^8), w = w_{16 L}^k
-  __host__ __device__ static constexpr int twoff(int s) {
-    int o = 0;
-    for (int i = 1; i < s; ++i) o += L(i) * 4;
-    return o;
-  }
-};
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-__device__ __forceinline__ int phys(int i) { return i + (i >> 5); }
-
-template <int R>
-__device__ __forceinline__ void codelet(float2* v);
-template <> __device__ __forceinline__ void codelet<2>(float2* v) { gb_dft2(v); }
-template <> __device__ __forceinline__ void codelet<4>(float2* v) { gb_dft4(v); }
-template <> __device__ __forceinline__ void codelet<8>(float2* v) { gb_dft8(v); }
-template <> __device__ __forceinline__ void codelet<16>(float2* v) { gb_dft16(v); }
-
-// the powers w^1..w^15 from (w, w^2, w^4, w^8), at most three products each
-__device__ __forceinline__ void powers16(float2* p, const float4* tw) {
-  const float4 a = __ldg(tw), b = __ldg(tw + 1);
-  p[1] = make_float2(a.x, a.y);
-  p[2] = make_float2(a.z, a.w);
-  p[4] = make_float2(b.x, b.y);
-  p[8] = make_float2(b.z, b.w);
-  p[3] = cmul(p[2], p[1]);
-  p[5] = cmul(p[4], p[1]);
-  p[6] = cmul(p[4], p[2]);
-  p[7] = cmul(p[4], p[3]);
-#pragma unroll
-  for (int r = 9; r < 16; ++r) p[r] = cmul(p[8], p[r - 8]);
-}
-
-__device__ __forceinline__ void twiddle16(float2* v, const float4* tw) {
-  float2 p[16];
-  powers16(p, tw);
-#pragma unroll
-  for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], p[r]);
-}
-
-// Stage S reads (+ twiddles + butterfly) for butterflies j = u + b*TPT of one
-// transform: from its padded exchange row, or (stage 0) from the landed tile
-// where element e sits at src[e * ESTRIDE].
-template <int LOGN, int S, bool FROM_TILE, int ESTRIDE>
-__device__ __forceinline__ void stage_in(float2* v, const float2* src, const float2* __restrict__ twt, int u,
-                                         int conj) {
-  using C = P2<LOGN>;
-  constexpr int R = C::radix(S), B = 16 / R, NB = C::N / R, L = C::L(S);
-#pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int j = u + b * C::TPT;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int idx = j + r * NB;
-      float2 x = FROM_TILE ? src[idx * ESTRIDE] : src[phys(idx)];
-      if (FROM_TILE && conj) x.y = -x.y;
-      v[b * R + r] = x;
-    }
-    if constexpr (L > 1) {
-      static_assert(R == 16, "twiddled stages are radix 16");
-      const int k = j & (L - 1);
-      twiddle16(v + b * R, reinterpret_cast<const float4*>(twt + C::twoff(S) + k * 4));
-    }
-    codelet<R>(v + b * R);
-  }
-}
-
-// Stage S writes to the padded exchange row
-template <int LOGN, int S>
-__device__ __forceinline__ void stage_out_x(const float2* v, float2* dst, int u) {
-  using C = P2<LOGN>;
-  constexpr int R = C::radix(S), B = 16 / R, L = C::L(S);
-#pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int j = u + b * C::TPT;
-    const int k = j & (L - 1);
-    const int base = (j - k) * R + k;
-#pragma unroll
-    for (int q = 0; q < R; ++q) dst[phys(base + q * L)] = v[b * R + q];
-  }
-}
-
-// Last stage writes global memory: output k = j + q*L of the transform goes
-// to dst[k * ostride].  POSTTW multiplies output k of column l2 by
-// w_N^{l2 k} = A[l2 L + j] * s^q with s = w_N^{l2 L} from B[l2] = (s, s^2, s^4, s^8).
-template <int LOGN, bool POSTTW>
-__device__ __forceinline__ void stage_out_g(const float2* v, float2* dst, int64_t ostride, int u, int conj,
-                                            const float2* __restrict__ A, const float2* __restrict__ Bt,
-                                            int64_t col) {
-  using C = P2<LOGN>;
-  constexpr int S = C::NST - 1;
-  constexpr int R = C::radix(S), B = 16 / R, L = C::L(S);
-#pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int j = u + b * C::TPT;  // j < L in the last stage
-    float2 p[16];
-    float2 a = make_float2(1.f, 0.f);
-    if constexpr (POSTTW) {
-      static_assert(R == 16, "post twiddles need a radix-16 last stage");
-      powers16(p, reinterpret_cast<const float4*>(Bt + col * 4));
-      a = __ldg(A + col * L + j);
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      float2 x = v[b * R + q];
-      if constexpr (POSTTW) x = cmul(x, q == 0 ? a : cmul(a, p[q]));
-      if (conj) x.y = -x.y;
-      dst[(int64_t)(j + q * L) * ostride] = x;
-    }
-  }
-}
-
-template <int LOGN, int S, bool POSTTW>
-__device__ __forceinline__ void later_stages(float2* v, float2* xrow_j, float2* xrow_s, float2* gout,
-                                             int64_t ostride, const float2* __restrict__ twt, int uj, int us,
-                                             int conj, bool valid, const float2* A, const float2* Bt, int64_t col) {
-  using C = P2<LOGN>;
-  if constexpr (S < C::NST) {
-    if constexpr (S == C::NST - 1) {
-      // the last stage runs in the store mapping
-      stage_in<LOGN, S, false, 1>(v, xrow_s, twt, us, conj);
-      if (valid) stage_out_g<LOGN, POSTTW>(v, gout, ostride, us, conj, A, Bt, col);
-    } else {
-      stage_in<LOGN, S, false, 1>(v, xrow_j, twt, uj, conj);
-      __syncthreads();
-      stage_out_x<LOGN, S>(v, xrow_j, uj);
-      __syncthreads();
-      later_stages<LOGN, S + 1, POSTTW>(v, xrow_j, xrow_s, gout, ostride, twt, uj, us, conj, valid, A, Bt, col);
-    }
-  }
-}
 
 // Thread -> (transform t, thread u within the transform):
 //   "j-fast": t = tid / TPT, u = tid % TPT (lanes along a transform)
@@ -332,20 +187,6 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static std::once_flag once;
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
 
 // Tensor map for the LOAD_ROWS tiles of k: 8-byte elements, dims (V0 columns,
 // n rows, the two vector loops by increasing stride), box (T, min(n, 256), 1, 1).
@@ -355,7 +196,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 void make_rows_map(const GbP2& k, int T, GbRowsMap* rm) {
   memset(rm, 0, sizeof(*rm));
   if (k.load != GB_P2_LOAD_ROWS || k.vis0 != 1) return;
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  PFN_cuTensorMapEncodeTiled_v12000 enc = (PFN_cuTensorMapEncodeTiled_v12000)gb_tensor_map_encoder();
   if (!enc || (reinterpret_cast<uintptr_t>(k.in) & 15)) return;
   const int64_t n = int64_t(1) << k.logn;
   struct D {
@@ -367,11 +208,11 @@ void make_rows_map(const GbP2& k, int T, GbRowsMap* rm) {
     std::swap(a, b);
     swap = 1;
   }
+  if (k.is <= 0 || (a.n > 1 && a.s <= 0) || (b.n > 1 && b.s <= 0)) return;
   cuuint64_t dim[4] = {(cuuint64_t)k.V0, (cuuint64_t)n, (cuuint64_t)a.n, (cuuint64_t)b.n};
   cuuint64_t str[3] = {(cuuint64_t)(k.is * 8), (cuuint64_t)a.s, (cuuint64_t)b.s};
   if (a.n == 1) str[1] = str[0] * n;  // extent-1 dims: any valid stride
   if (b.n == 1) str[2] = str[1] * a.n;
-  if (k.is <= 0 || a.s <= 0 || b.s <= 0) return;
   for (int i = 0; i < 3; ++i)
     if ((str[i] & 15) || str[i] >= (cuuint64_t(1) << 40)) return;
   if (str[0] < (cuuint64_t)(k.V0 * 8) || str[1] < str[0] || str[2] < str[1]) return;
@@ -570,6 +411,21 @@ cudaError_t dispatch(const GbP2& k, cudaStream_t st) {
 }
 
 }  // namespace
+
+void* gb_tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return reinterpret_cast<void*>(fn);
+}
 
 int gb_p2_supported(int logn, int load, int store, int posttw) {
   const bool cc = load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG;

@@ -180,3 +180,24 @@ def test_wisdom_decides_estimate_plan():
     assert "R=4.4.4" in explain([(64, 1, 1)])
     gbfft.fft_forget_wisdom()
     assert "R=16.4" in explain([(64, 1, 1)])
+
+
+def test_cluster_plans_and_wisdom():
+    """Contiguous 2^14..2^17 batches take the one-pass cluster kernel in
+    estimate mode; wisdom selects another instantiated (n1, n2, C) and rejects
+    configurations that are not built."""
+    for e in (14, 15, 16, 17):
+        n = 2 ** e
+        txt = explain([(n, 1, 1)], [(8, n, n)])
+        assert f"pass cluster n={n} = " in txt, txt
+    # strided transforms or two vector loops keep the four-step plan
+    assert "pass cluster" not in explain([(65536, 8, 8)], [(8, 1, 1)])
+    gbfft.fft_forget_wisdom()
+    key = "r1 n=65536 is=1 os=1 v=[(8,65536,65536)] ip=0"
+    gbfft.fft_import_wisdom(f"gbfft-wisdom 1\n{key}\tcluster:8.8.16.1\n")
+    assert "C=16 buffers=1" in explain([(65536, 1, 1)], [(8, 65536, 65536)])
+    for bad in ("cluster:9.9.9.1", "cluster:8.8.16", "cluster:7.9.8.1", "cluster:8.8.16.3"):
+        with pytest.raises(gbfft.GbfftError) as ei:
+            gbfft.fft_import_wisdom(f"gbfft-wisdom 1\n{key}\t{bad}\n")
+        assert ei.value.code == gbfft.FFT_ERR_WISDOM
+    gbfft.fft_forget_wisdom()
