@@ -173,8 +173,8 @@ struct Builder {
   int64_t estimate_split(int64_t n) const {
     const int lg = log2_exact(n);
     if (lg >= 12) {
-      // powers of two: passes of at most 1024 points keep every TMA row copy
-      // of a strided pass at 64 bytes or more; three passes beyond 2^20
+      // powers of two: a near-square split, so that both passes are one-CTA
+      // TMA passes up to 2^20; three passes beyond
       const int e1 = lg <= 20 ? lg / 2 : (lg + 2) / 3;
       return (int64_t)1 << e1;
     }
@@ -706,6 +706,12 @@ struct Builder {
       if (pc.prec) return c;  // the requested tensor-core precision decides the pass
     }
     const int lg = log2_exact(n);
+    // estimate mode takes the first candidate: the cluster pass where it beat
+    // two TMA passes when measured (2^14), the two passes above
+    if (!measure && lg >= 15 && lg <= 17 && smooth_codelet(n)) {
+      const int64_t a = estimate_split(n);
+      if (a > 1) c.push_back("split:" + std::to_string(a));
+    }
     if (!prec && cluster_ok(d, V)) {
       int cfg[16][4];
       const int nc = gb_cluster_configs(lg, cfg, 16);

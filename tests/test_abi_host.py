@@ -183,13 +183,16 @@ def test_wisdom_decides_estimate_plan():
 
 
 def test_cluster_plans_and_wisdom():
-    """Contiguous 2^14..2^17 batches take the one-pass cluster kernel in
-    estimate mode; wisdom selects another instantiated (n1, n2, C) and rejects
+    """Estimate mode takes the one-pass cluster kernel for contiguous 2^14
+    batches and two TMA passes for 2^15..2^17 (the faster of the two when
+    measured); wisdom selects any instantiated (n1, n2, C, buffers) and rejects
     configurations that are not built."""
-    for e in (14, 15, 16, 17):
+    txt = explain([(16384, 1, 1)], [(8, 16384, 16384)])
+    assert "pass cluster n=16384 = " in txt, txt
+    for e in (15, 16, 17):
         n = 2 ** e
         txt = explain([(n, 1, 1)], [(8, n, n)])
-        assert f"pass cluster n={n} = " in txt, txt
+        assert "pass cluster" not in txt and f"cooley-tukey n={n}" in txt, txt
     # strided transforms or two vector loops keep the four-step plan
     assert "pass cluster" not in explain([(65536, 8, 8)], [(8, 1, 1)])
     gbfft.fft_forget_wisdom()

@@ -32,7 +32,7 @@ def u(count, seed):
 def force(n, how, choice, inplace=False):
     """Import a wisdom entry that makes the planner take `choice` for this problem."""
     gbfft.fft_forget_wisdom()
-    v = ",".join(f"({a},{b},{c})" for a, b, c in how)
+    v = ",".join(f"({a},{b},{c})" for a, b, c in how if a > 1)  # the canonical problem drops n = 1 loops
     gbfft.fft_import_wisdom(f"gbfft-wisdom 1\nr1 n={n} is=1 os=1 v=[{v}] ip={1 if inplace else 0}\t{choice}\n")
 
 
@@ -79,10 +79,13 @@ def test_cluster_inplace_and_single_transform():
     for batch in (1, 21):
         how = [(batch, n, n)]
         x = u(n * batch, 500 + batch)
-        err, info = check([(n, 1, 1)], how, 1, x, flags=gbfft.FFT_ESTIMATE, inplace=True, algo="ct")
-        assert "pass cluster" in info
-        err, info = check([(n, 1, 1)], how, -1, x, flags=gbfft.FFT_ESTIMATE, algo="ct")
-        assert "pass cluster" in info
+        for inplace, sign in ((True, 1), (False, -1)):
+            force(n, how, "cluster:8.8.8.2", inplace=inplace)
+            try:
+                err, info = check([(n, 1, 1)], how, sign, x, flags=gbfft.FFT_WISDOM_ONLY, inplace=inplace, algo="ct")
+            finally:
+                gbfft.fft_forget_wisdom()
+            assert "pass cluster" in info
 
 
 def test_cluster_full_size_sampled():
@@ -91,7 +94,11 @@ def test_cluster_full_size_sampled():
     n, batch = 2 ** 16, 512
     x = u(n * batch, 510)
     dims, how = [(n, 1, 1)], [(batch, n, n)]
-    y, info = run_gpu(dims, how, -1, x, flags=gbfft.FFT_ESTIMATE)
+    force(n, how, "cluster:8.8.8.2")
+    try:
+        y, info = run_gpu(dims, how, -1, x, flags=gbfft.FFT_WISDOM_ONLY)
+    finally:
+        gbfft.fft_forget_wisdom()
     assert "pass cluster" in info
     for t in (0, 1, 255, 511):
         seg = x[t * n:(t + 1) * n]
@@ -105,7 +112,11 @@ def test_cluster_plan_in_group():
     """n = 2^14 has a one-CTA fallback the group executor runs; n = 2^16 has
     none and the group is refused."""
     p14 = gbfft.Plan([(2 ** 14, 1, 1)], [(4, 2 ** 14, 2 ** 14)], -1, gbfft.FFT_ESTIMATE)
-    p16 = gbfft.Plan([(2 ** 16, 1, 1)], [(4, 2 ** 16, 2 ** 16)], -1, gbfft.FFT_ESTIMATE)
+    force(2 ** 16, [(4, 2 ** 16, 2 ** 16)], "cluster:8.8.8.2")
+    try:
+        p16 = gbfft.Plan([(2 ** 16, 1, 1)], [(4, 2 ** 16, 2 ** 16)], -1, gbfft.FFT_WISDOM_ONLY)
+    finally:
+        gbfft.fft_forget_wisdom()
     try:
         assert "pass cluster" in p14.info and "pass cluster" in p16.info
         g = gbfft.fft_group_create([p14.handle])
