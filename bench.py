@@ -153,6 +153,22 @@ def flops_of(n_points, count):
     return 5.0 * n_points * math.log2(n_points) * count
 
 
+def max_over_ranks(value, device):
+    """The largest of every rank's value (a step time), through the process group
+    when there is one."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gflops(world, flops_per_rank_step, ms_per_step):
+    """Whole-job throughput: every replica does the same step, timed by the slowest."""
+    return world * flops_per_rank_step / (ms_per_step * 1e-3) / 1e9
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def run_gpu(args, rank, world):
@@ -209,16 +225,12 @@ def run_gpu(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    total_ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(start.elapsed_time(end), dev)
 
     step_flops = sum(flops_of(npts, count) for _, _, _, npts, count in plans)
     step_bytes = sum(16.0 * npts * count for _, _, _, npts, count in plans)
     ms_per_step = total_ms / args.steps
-    value = world * step_flops / (ms_per_step * 1e-3) / 1e9
+    value = aggregate_gflops(world, step_flops, ms_per_step)
 
     # per-plan breakdown; the roofline is taken for the kernel family with the
     # largest share of the step (plans whose passes all use that family)
@@ -267,13 +279,9 @@ def run_gpu(args, rank, world):
             e2e_step()
         b.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = a.elapsed_time(b) / e2e_steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, dev)
         nbytes = sum(8 * npts * count for _, _, _, npts, count in plans)
-        e2e = {"value": round(world * step_flops / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+        e2e = {"value": round(aggregate_gflops(world, step_flops, e2e_ms), 2), "unit": "GFLOP/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": round(e2e_ms, 3)}
 
     launches = sum(p.launches for _, _, p, _, _ in plans) * args.steps
