@@ -440,6 +440,122 @@ struct Builder {
     line(depth, o.str());
   }
 
+  // Mixed-radix TMA pass kernel (stockham_mr.cu): smooth lengths that are not
+  // powers of two, up to GB_MR_MAX_N points, at most two vector loops, tile
+  // shapes as for the power-of-two kernels.
+  struct MRChoice {
+    int load = -1, store = -1, T = 0, tpt = 0;
+    std::vector<int> rad;
+    Dim v0{1, 0, 0};
+    Dim rest{1, 0, 0};
+  };
+
+  static bool mr_choose(const Dim& d, const std::vector<Dim>& Vin, bool posttw, MRChoice* c) {
+    if (d.n < 2 || d.n > GB_MR_MAX_N || log2_exact(d.n) >= 0 || !smooth_codelet(d.n) || Vin.size() > 2) return false;
+    const std::vector<Dim> V = order_for_pass(Vin);
+    MRChoice ch;
+    ch.rad = default_radices(d.n);
+    if (ch.rad.size() < 2 || ch.rad.size() > GB_MR_MAX_ST) return false;
+    if (!V.empty()) ch.v0 = V[0];
+    if (V.size() > 1) ch.rest = V[1];
+    const Dim& v0 = ch.v0;
+    const bool rows_ok = v0.is == 1 && v0.n > 1;
+    const bool cols_ok = v0.os == 1 && v0.n > 1;
+    if (posttw) {
+      ch.load = rows_ok ? GB_P2_LOAD_ROWS : -1;
+      ch.store = cols_ok ? GB_P2_STORE_COLS : -1;
+    } else {
+      ch.load = d.is == 1 ? GB_P2_LOAD_CONTIG : (rows_ok ? GB_P2_LOAD_ROWS : -1);
+      ch.store = d.os == 1 ? GB_P2_STORE_CONTIG : (cols_ok ? GB_P2_STORE_COLS : -1);
+    }
+    if (ch.load < 0 || ch.store < 0) return false;
+    ch.tpt = gb_mr_threads((int)d.n, ch.rad.data(), (int)ch.rad.size());
+    if (ch.tpt > 512) return false;
+    ch.T = gb_mr_tile((int)d.n, ch.tpt, ch.load, ch.store, v0.n);
+    if (ch.T < 1) return false;
+    *c = ch;
+    return true;
+  }
+
+  void emit_mr(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t posttwN, int depth) {
+    MRChoice c;
+    if (!mr_choose(d, V, posttwN > 0, &c)) {
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    GbMR k{};
+    k.n = (int)d.n;
+    k.nst = (int)c.rad.size();
+    k.T = c.T;
+    k.tpt = c.tpt;
+    k.load = c.load;
+    k.store = c.store;
+    k.posttw = posttwN > 0 ? 1 : 0;
+    k.conj = conj;
+    int64_t L = 1;
+    for (int s = 0; s < k.nst; ++s) {
+      const int R = c.rad[s];
+      k.radix[s] = R;
+      k.L[s] = (int)L;
+      k.Lmagic[s] = L > 1 ? (unsigned)((uint64_t(1) << 32) / (uint64_t)L) : 0u;
+      if (s > 0) {
+        float2* t = (float2*)dalloc(sizeof(float2) * (size_t)(L * (R - 1)));
+        if (t && gb_make_full_stage_twiddles(t, L, R, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+        k.tw[s] = t;
+      }
+      L *= R;
+    }
+    k.V0 = c.v0.n;
+    k.vis0 = c.v0.is;
+    k.vos0 = c.v0.os;
+    k.is = d.is;
+    k.os = d.os;
+    k.nb1 = c.rest.n;
+    k.vis1 = c.rest.is;
+    k.vos1 = c.rest.os;
+    if (k.posttw) {
+      const float2 *lo = nullptr, *hi = nullptr;
+      int64_t S = 0;
+      split_roots(posttwN, &lo, &hi, &S);
+      k.ptw_lo = lo;
+      k.ptw_hi = hi;
+      k.ptwN = (unsigned)posttwN;
+      k.ptwS = (unsigned)S;
+      k.ptwSmagic = (unsigned)((uint64_t(1) << 32) / (uint64_t)S);
+    }
+    k.pitch = smem_pitch(d.n);
+    const int boxr = d.n < 256 ? (int)d.n : 256;
+    k.land = c.load == GB_P2_LOAD_ROWS ? (int)((d.n + boxr - 1) / boxr * boxr) : (int)d.n;
+    k.status = P->d_status;
+    if ((int64_t)gb_mr_smem(k) > smem_limit()) {
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    // the generic pass over the same sub-problem: what the group executor runs
+    const std::vector<Dim> VV = order_for_pass(V);
+    Dim v0{1, 0, 0};
+    if (!VV.empty()) v0 = VV[0];
+    PostTw tw2{posttwN};
+    Step s;
+    std::string desc;
+    if (!make_single(d, VV, src, dst, conj, estimate_cfg(d, v0, !VV.empty(), default_radices(d.n)),
+                     k.posttw ? &tw2 : nullptr, &s, &desc))
+      return;
+    s.kind = STEP_MR;
+    s.mr = k;
+    P->steps.push_back(s);
+    static const char* ln[] = {"contig", "rows"};
+    static const char* sn[] = {"contig", "cols"};
+    std::ostringstream o;
+    o << "pass mr-tma n=" << d.n << " R=";
+    for (size_t i = 0; i < c.rad.size(); ++i) o << (i ? "." : "") << c.rad[i];
+    o << " load=" << ln[c.load] << " store=" << sn[c.store] << " T=" << c.T << " tpt=" << c.tpt << " is=" << d.is
+      << " os=" << d.os << " tile=" << dims_str({c.v0}) << " rest=" << dims_str({c.rest})
+      << (k.posttw ? " post-twiddle w_" + std::to_string(posttwN) + "^(v0*k)" : std::string()) << (conj ? " conj" : "")
+      << " (group fallback: " << desc << ")";
+    line(depth, o.str());
+  }
+
   // One-pass cluster kernel (cluster.cu) for contiguous transforms of
   // 2^13..2^17 points, at most one vector loop.
   static bool cluster_ok(const Dim& d, const std::vector<Dim>& V) {
@@ -543,8 +659,12 @@ struct Builder {
     for (const Dim& v : Vs) V1.push_back(v);
     const Dim d1{n1, n2 * d.is, n2};
     P2Choice pc;
+    MRChoice mc;
     if (p2_choose(d1, V1, true, &pc) && order_for_pass(V1)[0].n == n2 && order_for_pass(V1)[0].os == 1) {
       emit_p2(d1, V1, src, S, conj, n, depth + 1);
+    } else if (!prec && n <= 0xffffffffLL && mr_choose(d1, V1, true, &mc) && order_for_pass(V1)[0].n == n2 &&
+               order_for_pass(V1)[0].os == 1) {
+      emit_mr(d1, V1, src, S, conj, n, depth + 1);
     } else {
       PassCfg c1 = estimate_cfg(d1, V1[0], true, default_radices(n1));
       PostTw tw{n};
@@ -730,6 +850,8 @@ struct Builder {
       const int64_t a = estimate_split(n);
       if (a > 1) c.push_back("split:" + std::to_string(a));
     }
+    MRChoice mc;
+    if (!prec && mr_choose(d, V, false, &mc)) c.push_back("mr");
     if (smooth_codelet(n)) {
       std::vector<int> rad = default_radices(n);
       if (single_pass_ok(n, rad)) {
@@ -857,6 +979,8 @@ struct Builder {
     if (err) return;
     if (choice == "p2") {
       emit_p2(d, V, src, dst, conj, 0, depth);
+    } else if (choice == "mr") {
+      emit_mr(d, V, src, dst, conj, 0, depth);
     } else if (choice.rfind("single:", 0) == 0) {
       PassCfg cfg;
       if (!cfg.parse(choice.substr(7))) {
@@ -955,6 +1079,13 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
       }
       else
         e = gb_launch_pass(s.pass, s.dpass, bufs[s.src], bufs[s.dst], s.threads, s.smem, s.grid, st);
+      break;
+    }
+    case STEP_MR: {
+      GbMR k = s.mr;
+      k.in = bufs[s.src];
+      k.out = bufs[s.dst];
+      e = gb_launch_mr(k, st);
       break;
     }
     case STEP_CLUSTER: {

@@ -74,6 +74,36 @@ int gb_cluster_configs(int logn, int (*cfg)[4], int max_cfg);
 int gb_cluster_max_active(int logn1, int logn2, int csize, int nbuf);
 cudaError_t gb_launch_cluster(const GbCluster& k, cudaStream_t st);
 
+// Mixed-radix pass kernel with TMA tiles (stockham_mr.cu): one Stockham pass
+// over transforms of any smooth length n <= GB_MR_MAX_N whose radix schedule
+// (2, 3, 4, 5, 7, 8, 9, 11, 13, 16) comes at run time.  Tile shapes as for
+// GbP2: LOAD_CONTIG / LOAD_ROWS, STORE_CONTIG / STORE_COLS; one extra vector
+// loop; optional four-step post twiddle w_N^{col * k} from two sqrt(N) tables.
+#define GB_MR_MAX_ST 8
+#define GB_MR_MAX_N 8192
+struct GbMR {
+  int n, nst, T, tpt;
+  int load, store, posttw, conj;
+  int radix[GB_MR_MAX_ST], L[GB_MR_MAX_ST];
+  unsigned Lmagic[GB_MR_MAX_ST];     // floor(2^32 / L) (quotients corrected once)
+  const float2* tw[GB_MR_MAX_ST];    // stage s >= 1: [k][R-1] = w_{L R}^{r k}
+  const float2* in;                  // set at execute time
+  float2* out;
+  int64_t V0, is, os, vis0, vos0;    // tile dimension: V0 transforms
+  int64_t nb1, vis1, vos1;           // one more vector loop
+  const float2* ptw_lo;              // post twiddle w_N^m = hi[m / S] * lo[m % S]
+  const float2* ptw_hi;
+  unsigned ptwN, ptwS, ptwSmagic;
+  int pitch;                         // padded exchange row (odd, in elements)
+  int land;                          // landing elements per transform (n, or rows rounded to boxes)
+  int* status;
+  int64_t grid;                      // <= 0: persistent grid sized by occupancy
+};
+int gb_mr_threads(int n, const int* radix, int nst);   // threads per transform (<= 16 values each)
+int gb_mr_tile(int n, int tpt, int load, int store, int64_t V0);  // transforms per tile (0: none fits)
+size_t gb_mr_smem(const GbMR& k);
+cudaError_t gb_launch_mr(const GbMR& k, cudaStream_t st);
+
 // Bluestein helper kernels for convolution lengths beyond one CTA (bluestein.cu).
 struct GbBlueIO {
   const float2* in;     // user input, element 0
@@ -125,6 +155,8 @@ cudaError_t gb_make_roots(float2* out, int64_t count, int64_t N, int64_t mult, c
 cudaError_t gb_make_chirp(float2* out, int64_t n, cudaStream_t st);
 // out[k*4 + i] = w_N^{p k N/(L R)} for k < L and p = 1, 2, 4, 8 (i = log2 p)
 cudaError_t gb_make_stage_twiddles(float2* out, int64_t N, int64_t L, int R, cudaStream_t st);
+// out[k*(R-1) + r-1] = w_{L R}^{r k} for k < L, 0 < r < R (mixed-radix stage tables)
+cudaError_t gb_make_full_stage_twiddles(float2* out, int64_t L, int R, cudaStream_t st);
 // four-step post twiddles w_N^{c k}, k = j + q L: A[c*L + j] = w_N^{c j},
 // B[c*4 + i] = w_N^{c L 2^i}, for c < ncols, j < L
 cudaError_t gb_make_posttw(float2* A, float2* B, int64_t N, int64_t ncols, int64_t L, cudaStream_t st);

@@ -42,7 +42,8 @@ enum StepKind {
   STEP_BLUE_MUL = 3,
   STEP_BLUE_POST = 4,
   STEP_POW2 = 5,
-  STEP_CLUSTER = 6
+  STEP_CLUSTER = 6,
+  STEP_MR = 7
 };
 
 // Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.
@@ -55,6 +56,7 @@ struct Step {
   GbP2 p2{};                      // STEP_POW2; pass/dpass hold the generic fallback
                                   // used when the input pointer is not 16-byte aligned
   GbCluster cl{};                 // STEP_CLUSTER; pass/dpass hold a one-CTA fallback where one exists
+  GbMR mr{};                      // STEP_MR; pass/dpass hold the generic pass (run by the group executor)
   GbCopy copy{};
   GbBlueIO blue{};
   int src = BUF_IN, dst = BUF_OUT;

@@ -53,7 +53,7 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
 
 // tiled tensor copy of one box through a tensor map (a __grid_constant__
 // kernel parameter); coordinates innermost first, x * element size a
-// multiple of 16 bytes
+// multiple of 16 bytes, the shared-memory destination on a 128-byte boundary
 __device__ __forceinline__ void tensor_copy_4d(uint32_t dst, const void* tmap, int x, int y, int z, int w,
                                                uint32_t bar) {
   asm volatile(

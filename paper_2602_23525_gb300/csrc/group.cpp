@@ -117,6 +117,7 @@ extern "C" fft_group fft_group_create(int nplans, const fft_plan* plans, unsigne
       switch (st.kind) {
         case STEP_PASS:
         case STEP_CLUSTER:  // a cluster pass contributes its one-CTA fallback, where it has one
+        case STEP_MR:       // a mixed-radix TMA pass contributes its generic pass
         case STEP_POW2: {  // a power-of-two pass contributes its generic fallback descriptor
           q.seg.kind = GB_SEG_PASS;
           q.seg.pass = st.dpass;

@@ -63,6 +63,17 @@ __global__ void gb_posttw_kernel(float2* A, float2* B, int64_t N, int64_t ncols,
   }
 }
 
+// full per-stage table [k][R-1]: w_{L R}^{r k} for k < L, r = 1 .. R-1
+__global__ void gb_full_stage_tw_kernel(float2* out, int64_t L, int R) {
+  const int64_t total = L * (R - 1);
+  const int64_t N = L * R;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t k = i / (R - 1), r = i - k * (R - 1) + 1;
+    out[i] = root64((int64_t)(((unsigned long long)(r * k)) % (unsigned long long)N), N);
+  }
+}
+
 // chirp w_k = exp(-pi i (k^2 mod 2n) / n), k < n   (Bluestein)
 __global__ void gb_chirp_kernel(float2* out, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -142,6 +153,12 @@ cudaError_t gb_make_roots(float2* out, int64_t count, int64_t N, int64_t mult, c
 cudaError_t gb_make_stage_twiddles(float2* out, int64_t N, int64_t L, int R, cudaStream_t st) {
   if (L <= 0) return cudaSuccess;
   gb_stage_tw_kernel<<<grid_for(L * 4), 256, 0, st>>>(out, N, L, R);
+  return cudaGetLastError();
+}
+
+cudaError_t gb_make_full_stage_twiddles(float2* out, int64_t L, int R, cudaStream_t st) {
+  if (L <= 0 || R < 2) return cudaSuccess;
+  gb_full_stage_tw_kernel<<<grid_for(L * (R - 1)), 256, 0, st>>>(out, L, R);
   return cudaGetLastError();
 }
 

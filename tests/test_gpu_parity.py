@@ -287,3 +287,49 @@ def test_small_transform_kernel(e, sign):
     x = u(n * b, 70 + e)
     err, info = check([(n, 1, 1)], [(b, n, n)], sign, x, flags=EST)
     assert "p2-tma" in info
+
+
+# ---------------------------------------------------------------- mixed-radix TMA kernel
+
+@pytest.mark.parametrize("n", [12, 60, 100, 240, 1000, 2187, 3125, 4374, 7000])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_mr_kernel_contiguous(n, sign):
+    """Mixed-radix lengths through the TMA pass kernel: several tiles and a
+    ragged last tile; odd lengths (whole 16-byte copies need an even tile)."""
+    b = max(3, 20000 // n) | 1
+    for bb in (b, b + 1):  # odd batch: ragged tile (plain loads for odd n); even: copy engine
+        x = u(n * bb, 700 + n + bb)
+        err, info = check([(n, 1, 1)], [(bb, n, n)], sign, x, flags=EST)
+        assert "pass mr-tma" in info, info
+
+
+def test_mr_kernel_layouts():
+    """Strided columns (tensor-map boxes, several boxes of 256 rows and a partial
+    one), non-adjacent transforms (one copy each / plain loads for odd n), an
+    8-byte aligned input (plain loads), and two vector loops."""
+    for n, cols in [(2187, 64), (300, 48), (45, 32)]:
+        x = u(n * cols * 2, 710 + n)
+        err, info = check([(n, cols, 1)], [(cols, 1, n), (2, n * cols, n * cols)], -1, x, flags=EST)
+        assert "pass mr-tma" in info and "load=rows" in info, info
+    for n, pad in [(1000, 8), (1125, 5)]:
+        b = 37
+        x = u((n + pad) * b, 720 + n)
+        err, info = check([(n, 1, 1)], [(b, n + pad, n)], 1, x, flags=EST)
+        assert "pass mr-tma" in info, info
+    n, b = 3000, 11
+    x = u(n * b + 1, 730)
+    err, info = check([(n, 1, 1)], [(b, n, n)], -1, x, flags=EST, in_offset=1)
+    assert "pass mr-tma" in info
+    n = 360
+    x = u(5 * (6 * (n + 7) + 3), 731)
+    err, info = check([(n, 1, 1)], [(6, n + 7, n), (5, 6 * (n + 7) + 3, 6 * n)], -1, x, flags=EST)
+    assert "pass mr-tma" in info
+
+
+def test_mr_kernel_fourstep_bluestein():
+    """Bluestein for a prime (m = 20160 = 140 x 144: mixed-radix four-step
+    passes with the post twiddle) and a mixed-radix four-step length."""
+    for n, b in [(10007, 3), (20160, 4)]:
+        x = u(n * b, 740 + n)
+        err, info = check([(n, 1, 1)], [(b, n, n)], -1, x, flags=EST, algo="ct")
+        assert "pass mr-tma" in info and "post-twiddle" in info, info
