@@ -384,7 +384,8 @@ def run_uneven(args):
         ins.append(x)
         outs.append(torch.empty_like(x))
         flops += flops_of(n, batch)
-    g = gbfft.fft_group_create([p.handle for p in plans])
+    g = gbfft.fft_group_create([p.handle for p in plans])  # executor chosen by timing both
+    mode = gbfft.fft_group_mode(g)
     s = torch.cuda.Stream()
     sp = s.cuda_stream
     ip, op = [t.data_ptr() for t in ins], [t.data_ptr() for t in outs]
@@ -404,11 +405,21 @@ def run_uneven(args):
     t_group = timed(lambda: gbfft.fft_group_execute(g, ip, op, sp))
     t_seq = timed(lambda: [gbfft.fft_execute(p.handle, i, o, sp) for p, i, o in zip(plans, ip, op)])
     status = gbfft.fft_group_status(g)
+    # each executor on its own, for the record
+    per_mode = {}
+    for name, fl in (("persistent queue", gbfft.FFT_GROUP_PERSISTENT), ("graph of plan launches",
+                                                                          gbfft.FFT_GROUP_GRAPH)):
+        gm = gbfft.fft_group_create([p.handle for p in plans], fl)
+        per_mode[name] = round(timed(lambda: gbfft.fft_group_execute(gm, ip, op, sp)), 4)
+        gbfft.fft_group_destroy(gm)
     nbytes = sum(16.0 * n * batch for n in fft_inputs.UNEVEN_SIZES)
     res = {"metric": METRIC, "workload": "uneven: sizes 1000, 2187, 3125, 7168, 10007, 65536 x 512, "
-           "2187/7168/65536 transposed, forward, one persistent launch", "unit": "GFLOP/s",
+           "2187/7168/65536 transposed, forward, one group execution", "unit": "GFLOP/s",
+           "executor_ms": per_mode,
            "group": {"ms": round(t_group, 4), "value": round(flops / (t_group * 1e-3) / 1e9, 1),
-                     "gbs_algorithmic": round(nbytes / (t_group * 1e-3) / 1e9, 1), "launches": 1,
+                     "gbs_algorithmic": round(nbytes / (t_group * 1e-3) / 1e9, 1),
+                     "launches": gbfft.fft_group_launches(g),
+                     "executor": "persistent queue" if mode == 1 else "graph of plan launches",
                      "status": status},
            "sequential": {"ms": round(t_seq, 4), "value": round(flops / (t_seq * 1e-3) / 1e9, 1),
                           "gbs_algorithmic": round(nbytes / (t_seq * 1e-3) / 1e9, 1),

@@ -178,37 +178,51 @@ void fft_forget_wisdom(void);
 /* ---------------------------------------------------------------- groups */
 
 /*
- * Uneven batches in one persistent launch.  A group holds several plans of
- * any kind and executes all of them together: one persistent kernel takes
- * (step, tile) work items from a device queue ordered by step level, each
- * item waiting (bounded, about 1 s) until the previous step of its own plan
- * has completed; a plan's power-of-two pass kernels are replaced there by its
- * generic pass over the same sub-problem, so each transform's result matches
- * executing its plan alone to within the library's rounding (not bit for bit).
+ * Uneven batches.  A group holds several plans of any kind and executes all
+ * of them together, with one of two executors, chosen at creation by timing
+ * both on buffers shaped like the plans' arrays (the measuring of sec. 4.3
+ * applied to the whole batch) unless a flag fixes it:
+ *   persistent queue (FFT_GROUP_PERSISTENT): one persistent kernel takes
+ *     (step, tile) work items from a device queue ordered by step level, each
+ *     item waiting (bounded, about 1 s) until the previous step of its own
+ *     plan has completed; a plan's specialised pass kernels are replaced there
+ *     by its generic pass over the same sub-problem, so each transform's
+ *     result matches executing its plan alone to within the library's
+ *     rounding (not bit for bit).  Plans with a step that has no generic
+ *     form (a cluster pass beyond one CTA) cannot use it.
+ *   graph of plan launches (FFT_GROUP_GRAPH): every plan's own kernels on one
+ *     of up to eight forked streams, joined back into the caller's stream and
+ *     captured into a CUDA graph (bit-identical to executing each plan alone).
  *   fft_group_create  : nplans >= 1 plans, kept by pointer (they must outlive
- *                       the group); flags 0 or FFT_GROUP_DEBUG_STALL.  NULL on
- *                       error (INVALID_ARG, UNSUPPORTED, OOM, CUDA).
+ *                       the group); flags 0, FFT_GROUP_PERSISTENT,
+ *                       FFT_GROUP_GRAPH, FFT_GROUP_DEBUG_STALL (implies the
+ *                       queue).  NULL on error (INVALID_ARG, UNSUPPORTED, OOM,
+ *                       CUDA).  Timing both executors synchronises the device.
  *   fft_group_execute : ins[i], outs[i] are the device arrays of plan i, with
  *                       the same rules as fft_execute.  On a non-default
- *                       stream the launch (counter reset + kernel) is captured
- *                       into a CUDA graph once and replayed afterwards; the
- *                       pointer table is rewritten only when pointers change.
- *                       Executions of one group must not overlap on the GPU.
+ *                       stream the work is captured into a CUDA graph once
+ *                       and replayed (the queue's pointer table is rewritten,
+ *                       the plan graph updated in place, when pointers
+ *                       change).  Executions of one group must not overlap.
  *   fft_group_status  : waits for the device, returns FFT_OK or
  *                       FFT_ERR_DEVICE_TIMEOUT if a wait gave up (and clears it).
- *   fft_group_launches: kernel launches per execution (1).
+ *   fft_group_launches: kernel launches per execution (1 for the queue).
+ *   fft_group_mode    : 1 persistent queue, 2 graph of plan launches.
  * FFT_GROUP_DEBUG_STALL adds one work item that waits on a segment no item
  * belongs to, with a 50 ms bound: for testing that a device wait that runs
  * out reports FFT_ERR_DEVICE_TIMEOUT and leaves the context usable.
- * The persistent executor has no counterpart in the paper; it serves the
- * vector loops of sec. 4.1 when the transforms of a batch differ in size.
+ * Neither executor has a counterpart in the paper; they serve the vector
+ * loops of sec. 4.1 when the transforms of a batch differ in size.
  */
 #define FFT_GROUP_DEBUG_STALL (1u << 8)
+#define FFT_GROUP_PERSISTENT (1u << 9)
+#define FFT_GROUP_GRAPH (1u << 10)
 typedef struct fft_group_s *fft_group;
 fft_group fft_group_create(int nplans, const fft_plan *plans, unsigned flags);
 int fft_group_execute(fft_group g, const void *const *ins, void *const *outs, void *stream);
 int fft_group_status(fft_group g);
 int fft_group_launches(fft_group g);
+int fft_group_mode(fft_group g);
 void fft_group_destroy(fft_group g);
 
 /* ---------------------------------------------------------------- serving */

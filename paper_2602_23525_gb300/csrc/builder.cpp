@@ -499,7 +499,7 @@ struct Builder {
       k.L[s] = (int)L;
       k.Lmagic[s] = L > 1 ? (unsigned)((uint64_t(1) << 32) / (uint64_t)L) : 0u;
       if (s > 0) {
-        float2* t = (float2*)dalloc(sizeof(float2) * (size_t)(L * (R - 1)));
+        float2* t = (float2*)dalloc(sizeof(float2) * (size_t)(L * (R & ~1)));
         if (t && gb_make_full_stage_twiddles(t, L, R, 0) != cudaSuccess) err = FFT_ERR_CUDA;
         k.tw[s] = t;
       }

@@ -86,7 +86,7 @@ struct GbMR {
   int load, store, posttw, conj;
   int radix[GB_MR_MAX_ST], L[GB_MR_MAX_ST];
   unsigned Lmagic[GB_MR_MAX_ST];     // floor(2^32 / L) (quotients corrected once)
-  const float2* tw[GB_MR_MAX_ST];    // stage s >= 1: [k][R-1] = w_{L R}^{r k}
+  const float2* tw[GB_MR_MAX_ST];    // stage s >= 1: [k][W] = w_{L R}^{r k}, W = even(R-1)
   const float2* in;                  // set at execute time
   float2* out;
   int64_t V0, is, os, vis0, vos0;    // tile dimension: V0 transforms
@@ -155,7 +155,8 @@ cudaError_t gb_make_roots(float2* out, int64_t count, int64_t N, int64_t mult, c
 cudaError_t gb_make_chirp(float2* out, int64_t n, cudaStream_t st);
 // out[k*4 + i] = w_N^{p k N/(L R)} for k < L and p = 1, 2, 4, 8 (i = log2 p)
 cudaError_t gb_make_stage_twiddles(float2* out, int64_t N, int64_t L, int R, cudaStream_t st);
-// out[k*(R-1) + r-1] = w_{L R}^{r k} for k < L, 0 < r < R (mixed-radix stage tables)
+// out[k*W + r-1] = w_{L R}^{r k} for k < L, 0 < r < R, W = R-1 rounded up to
+// even (mixed-radix stage tables; L*W entries, 16-byte rows)
 cudaError_t gb_make_full_stage_twiddles(float2* out, int64_t L, int R, cudaStream_t st);
 // four-step post twiddles w_N^{c k}, k = j + q L: A[c*L + j] = w_N^{c j},
 // B[c*4 + i] = w_N^{c L 2^i}, for c < ncols, j < L

@@ -6,8 +6,8 @@
 // switches once (uniformly across the CTA) to the generated straight-line
 // codelet of its radix (sec. 5), and each thread keeps at most 16 values per
 // stage in registers.  Stage s > 0 multiplies by w_{L R}^{r k} from a full
-// per-stage table [k][R-1] (sec. 6: accurate precomputed roots, no
-// recurrence); k = j mod L comes from a multiply-high by a precomputed
+// per-stage table [k][W], W = R-1 rounded up to even for 128-bit loads
+// (sec. 6: accurate precomputed roots, no recurrence); k = j mod L comes from a multiply-high by a precomputed
 // reciprocal with one correction step.
 //
 // Tiles and copies follow the power-of-two kernels (stockham_pow2.cu): a
@@ -94,9 +94,14 @@ __device__ __forceinline__ void stage_in(float2* v, const Src& src, int u, int t
       if (L > 1) {
         unsigned q, k;
         divmod_magic((unsigned)j, (unsigned)L, Lmagic, &q, &k);
-        const float2* t = tw + k * (R - 1);
+        constexpr int W = ((R - 1) + 1) & ~1;  // row length, even: 128-bit loads
+        const float4* t = reinterpret_cast<const float4*>(tw + k * W);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b * R + r] = cmulm(v[b * R + r], __ldg(t + r - 1));
+        for (int h = 0; h < W / 2; ++h) {
+          const float4 w = __ldg(t + h);
+          if (2 * h + 1 < R) v[b * R + 2 * h + 1] = cmulm(v[b * R + 2 * h + 1], make_float2(w.x, w.y));
+          if (2 * h + 2 < R) v[b * R + 2 * h + 2] = cmulm(v[b * R + 2 * h + 2], make_float2(w.z, w.w));
+        }
       }
       mr_codelet<R>(v + b * R);
     }
@@ -138,7 +143,7 @@ struct Dst {
   unsigned N, S, Smagic;
 };
 
-template <int R>
+template <int R, bool UNIT>
 __device__ __forceinline__ void stage_out_g(const float2* v, const Dst& d, int u, int tpt, int nb, int L,
                                             unsigned Lmagic) {
   constexpr int BMAX = 16 / R;
@@ -159,7 +164,8 @@ __device__ __forceinline__ void stage_out_g(const float2* v, const Dst& d, int u
           x = cmulm(x, cmulm(__ldg(d.hi + hi), __ldg(d.lo + lo)));
         }
         if (d.conj) x.y = -x.y;
-        d.p[(int64_t)idx * d.stride] = x;
+        if (UNIT) d.p[idx] = x;
+        else d.p[(int64_t)idx * d.stride] = x;
       }
     }
   }
@@ -173,7 +179,10 @@ __device__ __forceinline__ void run_stage(float2* v, const Src& src, float2* xro
   if (valid) stage_in<R>(v, src, u, tpt, nb, L, Lmagic, tw);
   if (sync_mid) __syncthreads();
   if (valid) {
-    if (dst) stage_out_g<R>(v, *dst, u, tpt, nb, L, Lmagic);
+    if (dst) {
+      if (dst->stride == 1) stage_out_g<R, true>(v, *dst, u, tpt, nb, L, Lmagic);
+      else stage_out_g<R, false>(v, *dst, u, tpt, nb, L, Lmagic);
+    }
     else stage_out_x<R>(v, xrow, u, tpt, nb, L, Lmagic);
   }
 }
@@ -433,8 +442,12 @@ int gb_mr_tile(int n, int tpt, int load, int store, int64_t V0) {
   const bool cols = load == GB_P2_LOAD_ROWS || store == GB_P2_STORE_COLS;
   const int tmin = load == GB_P2_LOAD_ROWS ? 2 : 1;  // strided tiles: 16-byte box rows
   const bool odd_contig = !cols && (n % 2) != 0;
+  // 256-thread CTAs (two per SM) unless a transform needs more threads or
+  // the tile shape needs a wider CTA (an even tile for odd lengths or
+  // strided loads)
+  const int tmax = (tpt * tmin <= 256 && !(odd_contig && 2 * tpt > 256)) ? 256 / tpt : 512 / tpt;
   for (int pass = 0; pass < 2; ++pass) {
-    for (int T = 512 / tpt; T >= 1; --T) {
+    for (int T = tmax; T >= 1; --T) {
       const int64_t cap = (pass == 0 && odd_contig && T == 2) ? 8192 : 4096;
       if ((int64_t)T * n > cap && T > tmin) continue;
       if (cols && (V0 % T != 0 || (load == GB_P2_LOAD_ROWS && T % 2 != 0))) continue;

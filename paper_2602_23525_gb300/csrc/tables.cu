@@ -63,14 +63,16 @@ __global__ void gb_posttw_kernel(float2* A, float2* B, int64_t N, int64_t ncols,
   }
 }
 
-// full per-stage table [k][R-1]: w_{L R}^{r k} for k < L, r = 1 .. R-1
+// full per-stage table [k][W]: w_{L R}^{r k} at [k][r-1] for k < L, r = 1 .. R-1,
+// rows of W = R-1 rounded up to even entries (the padding entry is 1)
 __global__ void gb_full_stage_tw_kernel(float2* out, int64_t L, int R) {
-  const int64_t total = L * (R - 1);
+  const int64_t W = R & ~1;  // (R - 1) rounded up to even
+  const int64_t total = L * W;
   const int64_t N = L * R;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int64_t k = i / (R - 1), r = i - k * (R - 1) + 1;
-    out[i] = root64((int64_t)(((unsigned long long)(r * k)) % (unsigned long long)N), N);
+    const int64_t k = i / W, r = i - k * W + 1;
+    out[i] = r < R ? root64((int64_t)(((unsigned long long)(r * k)) % (unsigned long long)N), N) : make_float2(1.f, 0.f);
   }
 }
 
@@ -158,7 +160,7 @@ cudaError_t gb_make_stage_twiddles(float2* out, int64_t N, int64_t L, int R, cud
 
 cudaError_t gb_make_full_stage_twiddles(float2* out, int64_t L, int R, cudaStream_t st) {
   if (L <= 0 || R < 2) return cudaSuccess;
-  gb_full_stage_tw_kernel<<<grid_for(L * (R - 1)), 256, 0, st>>>(out, L, R);
+  gb_full_stage_tw_kernel<<<grid_for(L * (R & ~1)), 256, 0, st>>>(out, L, R);
   return cudaGetLastError();
 }
 

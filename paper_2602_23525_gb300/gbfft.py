@@ -40,6 +40,8 @@ FFT_PREC_TC_FP16 = 1 << 4
 FFT_PREC_TC_BF16 = 1 << 5
 FFT_PREC_SPLIT = 1 << 6
 FFT_GROUP_DEBUG_STALL = 1 << 8
+FFT_GROUP_PERSISTENT = 1 << 9
+FFT_GROUP_GRAPH = 1 << 10
 
 
 class fft_iodim(ctypes.Structure):
@@ -81,6 +83,7 @@ _SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "fft_group_status": (ctypes.c_int, [ctypes.c_void_p]),
     "fft_group_launches": (ctypes.c_int, [ctypes.c_void_p]),
+    "fft_group_mode": (ctypes.c_int, [ctypes.c_void_p]),
     "fft_group_destroy": (None, [ctypes.c_void_p]),
     "fft_server_create": (ctypes.c_void_p, [ctypes.c_size_t, ctypes.c_int, ctypes.c_uint]),
     "fft_server_now": (ctypes.c_double, [ctypes.c_void_p]),
@@ -241,6 +244,11 @@ def fft_group_status(group) -> int:
 
 def fft_group_launches(group) -> int:
     return load().fft_group_launches(group)
+
+
+def fft_group_mode(group) -> int:
+    """1: persistent queue, 2: graph of plan launches."""
+    return load().fft_group_mode(group)
 
 
 def fft_group_destroy(group) -> None:

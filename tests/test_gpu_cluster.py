@@ -109,8 +109,8 @@ def test_cluster_full_size_sampled():
 
 
 def test_cluster_plan_in_group():
-    """n = 2^14 has a one-CTA fallback the group executor runs; n = 2^16 has
-    none and the group is refused."""
+    """n = 2^14 has a one-CTA fallback the persistent queue runs; n = 2^16 has
+    none: the queue is refused and the group uses the graph of plan launches."""
     p14 = gbfft.Plan([(2 ** 14, 1, 1)], [(4, 2 ** 14, 2 ** 14)], -1, gbfft.FFT_ESTIMATE)
     force(2 ** 16, [(4, 2 ** 16, 2 ** 16)], "cluster:8.8.8.2")
     try:
@@ -119,11 +119,25 @@ def test_cluster_plan_in_group():
         gbfft.fft_forget_wisdom()
     try:
         assert "pass cluster" in p14.info and "pass cluster" in p16.info
-        g = gbfft.fft_group_create([p14.handle])
+        g = gbfft.fft_group_create([p14.handle], gbfft.FFT_GROUP_PERSISTENT)
         gbfft.fft_group_destroy(g)
         with pytest.raises(gbfft.GbfftError) as ei:
-            gbfft.fft_group_create([p16.handle])
+            gbfft.fft_group_create([p16.handle], gbfft.FFT_GROUP_PERSISTENT)
         assert ei.value.code == gbfft.FFT_ERR_UNSUPPORTED
+        g = gbfft.fft_group_create([p14.handle, p16.handle])
+        assert gbfft.fft_group_mode(g) == 2
+        x = fft_inputs.uniform_c64(4 * 2 ** 16, 520)
+        a = torch.from_numpy(x[:4 * 2 ** 14]).cuda()
+        b = torch.from_numpy(x).cuda()
+        ya, yb = torch.zeros_like(a), torch.zeros_like(b)
+        gbfft.fft_group_execute(g, [a.data_ptr(), b.data_ptr()], [ya.data_ptr(), yb.data_ptr()],
+                                torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert gbfft.fft_group_status(g) == gbfft.FFT_OK
+        gbfft.fft_group_destroy(g)
+        for y, xs, n in ((ya, x[:4 * 2 ** 14], 2 ** 14), (yb, x, 2 ** 16)):
+            ref = reference([(n, 1, 1)], [(4, n, n)], -1, xs, algo="ct")
+            assert per_transform_error(y.cpu().numpy(), ref, [(n, 1, 1)], [(4, n, n)]).max() <= TOL
     finally:
         p14.destroy()
         p16.destroy()

@@ -1,7 +1,9 @@
-"""Uneven batches in one persistent launch (fft_group_*): every transform of
-every plan matches the FP64 oracle (relative L2 <= 2e-6) and its own plan run
-alone; CUDA-graph replays and pointer changes keep results; a device wait that
-runs out reports FFT_ERR_DEVICE_TIMEOUT and leaves the context usable."""
+"""Uneven batches (fft_group_*), with each executor (persistent queue, graph
+of plan launches) and the measured choice: every transform of every plan
+matches the FP64 oracle (relative L2 <= 2e-6) and its own plan run alone (bit
+for bit with the graph of plan launches); CUDA-graph replays and pointer
+changes keep results; a device wait that runs out reports
+FFT_ERR_DEVICE_TIMEOUT and leaves the context usable."""
 import numpy as np
 import pytest
 
@@ -55,25 +57,35 @@ def run_group(probs, sign, stream, flags=0, repeat=1):
     return res
 
 
+MODES = [gbfft.FFT_GROUP_PERSISTENT, gbfft.FFT_GROUP_GRAPH, 0]
+
+
 @pytest.mark.parametrize("sign", [-1, 1])
-def test_uneven_group_matches_oracle_and_alone(sign):
+@pytest.mark.parametrize("flags", MODES)
+def test_uneven_group_matches_oracle_and_alone(sign, flags):
     probs = uneven_problems(8)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        outs, alone, status = run_group(probs, sign, s.cuda_stream, repeat=2)
+        outs, alone, status = run_group(probs, sign, s.cuda_stream, flags=flags, repeat=2)
     assert status == gbfft.FFT_OK
     for (n, dims, how, x), y, a in zip(probs, outs, alone):
         ref = reference(dims, how, sign, x, algo="ct" if n > 4096 else "auto")
         err = per_transform_error(y, ref, dims, how)
         assert err.max() <= TOL, (n, err.max())
         assert per_transform_error(y, a.astype(np.complex128), dims, how).max() <= TOL
+        if flags == gbfft.FFT_GROUP_GRAPH:
+            assert np.array_equal(y, a)
 
 
-def test_group_on_legacy_stream_and_pointer_change():
+@pytest.mark.parametrize("flags", MODES)
+def test_group_on_legacy_stream_and_pointer_change(flags):
     probs = uneven_problems(4)[:4]
     plans = [gbfft.Plan(d, h, -1, EST) for _, d, h, _ in probs]
     ins = [torch.from_numpy(x).cuda() for *_, x in probs]
-    g = gbfft.fft_group_create([p.handle for p in plans])
+    g = gbfft.fft_group_create([p.handle for p in plans], flags)
+    mode = gbfft.fft_group_mode(g)
+    assert mode == {gbfft.FFT_GROUP_PERSISTENT: 1, gbfft.FFT_GROUP_GRAPH: 2}.get(flags, mode) and mode in (1, 2)
+    assert gbfft.fft_group_launches(g) == (1 if mode == 1 else sum(p.launches for p in plans))
     s = torch.cuda.Stream()
     results = []
     for stream in (0, s.cuda_stream, s.cuda_stream):
