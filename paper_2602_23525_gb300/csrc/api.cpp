@@ -157,7 +157,7 @@ extern "C" int fft_import_wisdom(const char* text) {
     if (tab == std::string::npos || tab == 0 || tab + 1 >= line.size()) return set_err(FFT_ERR_WISDOM);
     const std::string key = line.substr(0, tab), val = line.substr(tab + 1);
     if (key.rfind("r1 ", 0) != 0) return set_err(FFT_ERR_WISDOM);
-    if (val == "p2" || val == "mr") {
+    if (val == "p2" || val == "mr" || val == "xpose") {
     } else if (val.rfind("single:", 0) == 0) {
       PassCfg c;
       if (!c.parse(val.substr(7))) return set_err(FFT_ERR_WISDOM);

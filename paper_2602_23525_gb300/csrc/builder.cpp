@@ -556,6 +556,38 @@ struct Builder {
     line(depth, o.str());
   }
 
+  // "transpose first" applies to an out-of-place transform whose output is
+  // contiguous per transform while its input is strided with a unit-stride
+  // vector loop; all output strides non-negative (the scratch copy of the
+  // output layout starts at element 0)
+  static bool xpose_ok(const Dim& d, const std::vector<Dim>& V) {
+    if (d.os != 1 || d.is == 1 || d.is == 0 || V.empty() || V.size() > 3) return false;
+    bool unit_in = false;
+    for (const Dim& v : V) {
+      if (v.os <= 0) return false;
+      if (v.is == 1) unit_in = true;
+    }
+    return unit_in;
+  }
+
+  void emit_xpose(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int depth) {
+    if (!xpose_ok(d, V) || src == dst) {
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    int64_t lo = 0, hi = 0;
+    footprint({d}, V, false, &lo, &hi);
+    line(depth, "transpose first: the input into the output's layout, then the transform (sec. 4.2.4 copy + sec. 4.2)");
+    const int S = new_scratch((size_t)(hi + 1) * sizeof(float2));
+    std::vector<Dim> W;
+    W.push_back({d.n, d.is, d.os});
+    for (const Dim& v : V) W.push_back(v);
+    emit_copy(canon_vec(W), src, S, depth + 1);
+    std::vector<Dim> V2;
+    for (const Dim& v : V) V2.push_back({v.n, v.os, v.os});
+    solve_rank1({d.n, d.os, d.os}, V2, S, dst, conj, depth + 1);
+  }
+
   // One-pass cluster kernel (cluster.cu) for contiguous transforms of
   // 2^13..2^17 points, at most one vector loop.
   static bool cluster_ok(const Dim& d, const std::vector<Dim>& V) {
@@ -820,6 +852,11 @@ struct Builder {
       v0 = V[tile_dim(V)];
       has_v = true;
     }
+    // transpose first: a batch-fastest input into the output's layout, then
+    // the same-layout transform (estimate mode: long lengths, where the
+    // strided tiles get thin)
+    const bool xpose = !prec && xpose_ok(d, V);
+    if (xpose && !measure && n >= 4096) c.push_back("xpose");
     P2Choice pc;
     if (p2_choose(d, V, false, &pc, prec)) {
       c.push_back("p2");
@@ -904,6 +941,7 @@ struct Builder {
         }
       }
     }
+    if (xpose && measure) c.push_back("xpose");
     if (!smooth_codelet(n) || c.empty()) c.push_back("blue:" + std::to_string(bluestein_length(n)));
     std::vector<std::string> u;
     for (const std::string& x : c)
@@ -981,6 +1019,8 @@ struct Builder {
       emit_p2(d, V, src, dst, conj, 0, depth);
     } else if (choice == "mr") {
       emit_mr(d, V, src, dst, conj, 0, depth);
+    } else if (choice == "xpose") {
+      emit_xpose(d, V, src, dst, conj, depth);
     } else if (choice.rfind("single:", 0) == 0) {
       PassCfg cfg;
       if (!cfg.parse(choice.substr(7))) {

@@ -365,6 +365,44 @@ __global__ void gb_copy_kernel(const GbCopy c) {
     gb_copy_elem(c, c.in, c.out, i, 0);
 }
 
+// Rank-0 copy that transposes: dims da (unit input stride) and db (unit
+// output stride) are moved through a 32 x 32 shared-memory tile so that both
+// the loads (lanes along da) and the stores (lanes along db) coalesce; every
+// other dimension is a batch loop.  Tiles are taken grid-stride.
+__global__ void __launch_bounds__(256) gb_transpose_kernel(const GbCopy c, int da, int db) {
+  __shared__ float2 tile[32][33];
+  const int64_t na = c.vn[da], nb = c.vn[db];
+  const int64_t ta_n = (na + 31) / 32, tb_n = (nb + 31) / 32;
+  const int64_t nrest = c.total / (na * nb);
+  const int64_t ntiles = ta_n * tb_n * nrest;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t ta = t % ta_n, r1 = t / ta_n, tb = r1 % tb_n;
+    int64_t rest = r1 / tb_n, rin = 0, rout = 0;
+    for (int d = c.nv - 1; d >= 0; --d) {
+      if (d == da || d == db) continue;
+      const int64_t q = rest / c.vn[d], k = rest - q * c.vn[d];
+      rest = q;
+      rin += k * c.vis[d];
+      rout += k * c.vos[d];
+    }
+    const int64_t ia = ta * 32 + tx;
+#pragma unroll
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t ib = tb * 32 + k;
+      if (ia < na && ib < nb) tile[k][tx] = __ldg(c.in + rin + ia * c.vis[da] + ib * c.vis[db]);
+    }
+    __syncthreads();
+    const int64_t ib = tb * 32 + tx;
+#pragma unroll
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t ja = ta * 32 + k;
+      if (ja < na && ib < nb) c.out[rout + ja * c.vos[da] + ib * c.vos[db]] = tile[tx][k];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 int gb_pass_max_smem_optin(void) {
@@ -439,6 +477,19 @@ cudaError_t gb_launch_group(const GbGroupArgs& a, int threads, size_t smem, int6
 
 cudaError_t gb_launch_copy(const GbCopy& c, cudaStream_t st) {
   if (c.total <= 0) return cudaSuccess;
+  // a transposing copy: one dimension is unit-stride on the input side, another
+  // on the output side
+  int da = -1, db = -1;
+  for (int d = 0; d < c.nv; ++d) {
+    if (c.vis[d] == 1 && c.vn[d] > 1) da = d;
+    if (c.vos[d] == 1 && c.vn[d] > 1) db = d;
+  }
+  if (da >= 0 && db >= 0 && da != db && c.vn[da] >= 8 && c.vn[db] >= 8) {
+    const int64_t tiles = ((c.vn[da] + 31) / 32) * ((c.vn[db] + 31) / 32) * (c.total / (c.vn[da] * c.vn[db]));
+    int64_t blocks = tiles < 152 * 8 ? tiles : 152 * 8;
+    gb_transpose_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, da, db);
+    return cudaGetLastError();
+  }
   int64_t blocks = (c.total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   gb_copy_kernel<<<(unsigned)blocks, 256, 0, st>>>(c);

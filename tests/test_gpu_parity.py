@@ -333,3 +333,30 @@ def test_mr_kernel_fourstep_bluestein():
         x = u(n * b, 740 + n)
         err, info = check([(n, 1, 1)], [(b, n, n)], -1, x, flags=EST, algo="ct")
         assert "pass mr-tma" in info and "post-twiddle" in info, info
+
+
+# ---------------------------------------------------------------- transpose first
+
+def test_rank0_transposes_bit_exact():
+    """Rank-0 copies that transpose go through the tiled transpose kernel:
+    ragged tiles, a batch loop, padded strides; results are bit-exact."""
+    for r, c in [(37, 41), (64, 64), (1000, 9), (9, 1000)]:
+        x = u(r * c, 900 + r)
+        y, _ = run_gpu([], [(r, c, 1), (c, 1, r)], -1, x, flags=EST)
+        assert np.array_equal(y.reshape(c, r), x.reshape(r, c).T), (r, c)
+    r, c, b = 33, 70, 3
+    x = u(b * (r * c + 5), 910)
+    y, _ = run_gpu([], [(r, c, 1), (c, 1, r), (b, r * c + 5, r * c)], 1, x, flags=EST)
+    for k in range(b):
+        src = x[k * (r * c + 5):k * (r * c + 5) + r * c].reshape(r, c)
+        assert np.array_equal(y[k * r * c:(k + 1) * r * c].reshape(c, r), src.T)
+
+
+@pytest.mark.parametrize("n,b", [(4096, 24), (7168, 40), (65536, 8), (12288, 16)])
+def test_transpose_first_plans(n, b):
+    """Transposed batches of long transforms: the input is copied into the
+    output's layout first, then transformed with the same-layout kernels."""
+    x = u(n * (b + 3), 920 + n)
+    for is_ in (b, b + 3):  # dense and padded input rows
+        err, info = check([(n, is_, 1)], [(b, 1, n)], -1, x, flags=EST, algo="ct")
+        assert "transpose first" in info, info
