@@ -942,7 +942,16 @@ struct Builder {
       }
     }
     if (xpose && measure) c.push_back("xpose");
-    if (!smooth_codelet(n) || c.empty()) c.push_back("blue:" + std::to_string(bluestein_length(n)));
+    if (!smooth_codelet(n) || c.empty()) {
+      // the convolution length: the smallest 2^a 3^b 5^c 7^d >= 2n - 1, and
+      // (measure mode) the next power of two, whose passes run on the
+      // power-of-two kernels
+      const int64_t m = bluestein_length(n);
+      c.push_back("blue:" + std::to_string(m));
+      int64_t m2 = 1;
+      while (m2 < 2 * n - 1) m2 <<= 1;
+      if (measure && m2 != m) c.push_back("blue:" + std::to_string(m2));
+    }
     std::vector<std::string> u;
     for (const std::string& x : c)
       if (std::find(u.begin(), u.end(), x) == u.end()) u.push_back(x);
