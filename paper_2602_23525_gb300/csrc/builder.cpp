@@ -450,12 +450,32 @@ struct Builder {
     Dim rest{1, 0, 0};
   };
 
+  // the prime factor of n beyond the codelet radices, if it is the only one
+  // and lies in 17..61 (the generic O(p^2) stage); 0 for smooth n, -1 else
+  static int generic_prime(int64_t n) {
+    for (int p : {2, 3, 5, 7, 11, 13})
+      while (n % p == 0) n /= p;
+    if (n == 1) return 0;
+    if (n < 17 || n > 61) return -1;
+    for (int64_t f = 2; f * f <= n; ++f)
+      if (n % f == 0) return -1;
+    return (int)n;
+  }
+
   static bool mr_choose(const Dim& d, const std::vector<Dim>& Vin, bool posttw, MRChoice* c) {
-    if (d.n < 2 || d.n > GB_MR_MAX_N || log2_exact(d.n) >= 0 || !smooth_codelet(d.n) || Vin.size() > 2) return false;
+    if (d.n < 2 || d.n > GB_MR_MAX_N || log2_exact(d.n) >= 0 || Vin.size() > 2) return false;
+    const int gp = generic_prime(d.n);
+    if (gp < 0) return false;
     const std::vector<Dim> V = order_for_pass(Vin);
     MRChoice ch;
-    ch.rad = default_radices(d.n);
-    if (ch.rad.size() < 2 || ch.rad.size() > GB_MR_MAX_ST) return false;
+    if (gp) {
+      ch.rad.push_back(gp);
+      if (d.n > gp)
+        for (int R : default_radices(d.n / gp)) ch.rad.push_back(R);
+    } else {
+      ch.rad = default_radices(d.n);
+    }
+    if (ch.rad.empty() || ch.rad.size() > GB_MR_MAX_ST || (ch.rad.size() < 2 && !gp)) return false;
     if (!V.empty()) ch.v0 = V[0];
     if (V.size() > 1) ch.rest = V[1];
     const Dim& v0 = ch.v0;
@@ -469,6 +489,8 @@ struct Builder {
       ch.store = d.os == 1 ? GB_P2_STORE_CONTIG : (cols_ok ? GB_P2_STORE_COLS : -1);
     }
     if (ch.load < 0 || ch.store < 0) return false;
+    // a single stage loads and stores with one thread mapping
+    if (ch.rad.size() == 1 && (ch.load == GB_P2_LOAD_ROWS) != (ch.store == GB_P2_STORE_COLS)) return false;
     ch.tpt = gb_mr_threads((int)d.n, ch.rad.data(), (int)ch.rad.size());
     if (ch.tpt > 512) return false;
     ch.T = gb_mr_tile((int)d.n, ch.tpt, ch.load, ch.store, v0.n);
@@ -523,6 +545,11 @@ struct Builder {
       k.ptwS = (unsigned)S;
       k.ptwSmagic = (unsigned)((uint64_t(1) << 32) / (uint64_t)S);
     }
+    if (c.rad[0] > 16) {
+      float2* w = (float2*)dalloc(sizeof(float2) * (size_t)c.rad[0]);
+      if (w && gb_make_roots(w, c.rad[0], c.rad[0], 1, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+      k.wp = w;
+    }
     k.pitch = smem_pitch(d.n);
     const int boxr = d.n < 256 ? (int)d.n : 256;
     k.land = c.load == GB_P2_LOAD_ROWS ? (int)((d.n + boxr - 1) / boxr * boxr) : (int)d.n;
@@ -531,16 +558,20 @@ struct Builder {
       err = FFT_ERR_WISDOM;
       return;
     }
-    // the generic pass over the same sub-problem: what the group executor runs
+    // the generic pass over the same sub-problem: what the persistent group
+    // queue runs (none for a prime radix beyond the codelets)
     const std::vector<Dim> VV = order_for_pass(V);
     Dim v0{1, 0, 0};
     if (!VV.empty()) v0 = VV[0];
     PostTw tw2{posttwN};
     Step s;
-    std::string desc;
-    if (!make_single(d, VV, src, dst, conj, estimate_cfg(d, v0, !VV.empty(), default_radices(d.n)),
+    std::string desc = "none";
+    if (c.rad[0] <= 16 &&
+        !make_single(d, VV, src, dst, conj, estimate_cfg(d, v0, !VV.empty(), default_radices(d.n)),
                      k.posttw ? &tw2 : nullptr, &s, &desc))
       return;
+    s.src = src;
+    s.dst = dst;
     s.kind = STEP_MR;
     s.mr = k;
     P->steps.push_back(s);

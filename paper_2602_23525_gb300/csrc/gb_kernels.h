@@ -75,8 +75,9 @@ int gb_cluster_max_active(int logn1, int logn2, int csize, int nbuf);
 cudaError_t gb_launch_cluster(const GbCluster& k, cudaStream_t st);
 
 // Mixed-radix pass kernel with TMA tiles (stockham_mr.cu): one Stockham pass
-// over transforms of any smooth length n <= GB_MR_MAX_N whose radix schedule
-// (2, 3, 4, 5, 7, 8, 9, 11, 13, 16) comes at run time.  Tile shapes as for
+// over transforms of length n <= GB_MR_MAX_N whose radix schedule (2, 3, 4,
+// 5, 7, 8, 9, 11, 13, 16, and as the first stage one prime 17..61 computed by
+// the generic O(R^2) DFT) comes at run time.  Tile shapes as for
 // GbP2: LOAD_CONTIG / LOAD_ROWS, STORE_CONTIG / STORE_COLS; one extra vector
 // loop; optional four-step post twiddle w_N^{col * k} from two sqrt(N) tables.
 #define GB_MR_MAX_ST 8
@@ -94,6 +95,7 @@ struct GbMR {
   const float2* ptw_lo;              // post twiddle w_N^m = hi[m / S] * lo[m % S]
   const float2* ptw_hi;
   unsigned ptwN, ptwS, ptwSmagic;
+  const float2* wp;                  // stage 0 of radix > 16 (a prime 17..61): w_R^m, m < R
   int pitch;                         // padded exchange row (odd, in elements)
   int land;                          // landing elements per transform (n, or rows rounded to boxes)
   int* status;

@@ -2,7 +2,8 @@
 //
 // The Stockham stages of eq. (2) (n1 = L, n2 = R at every stage, output
 // auto-sorted, sec. 2) for any length n = R_0 R_1 ... with radices 2, 3, 4,
-// 5, 7, 8, 9, 11, 13, 16: the schedule is a run-time parameter, every stage
+// 5, 7, 8, 9, 11, 13, 16 (and a first stage of one prime 17..61 by the
+// generic O(R^2) DFT): the schedule is a run-time parameter, every stage
 // switches once (uniformly across the CTA) to the generated straight-line
 // codelet of its radix (sec. 5), and each thread keeps at most 16 values per
 // stage in registers.  Stage s > 0 multiplies by w_{L R}^{r k} from a full
@@ -142,6 +143,67 @@ struct Dst {
   const float2* hi;
   unsigned N, S, Smagic;
 };
+
+// one output of the last stage to global memory
+__device__ __forceinline__ void store_g(const Dst& d, int idx, float2 x) {
+  if (d.posttw) {
+    const unsigned m = d.col * (unsigned)idx;
+    unsigned hi, lo;
+    divmod_magic(m, d.S, d.Smagic, &hi, &lo);
+    x = cmulm(x, cmulm(__ldg(d.hi + hi), __ldg(d.lo + lo)));
+  }
+  if (d.conj) x.y = -x.y;
+  d.p[(int64_t)idx * d.stride] = x;
+}
+
+// Stage 0 of a prime radix R in 17..61 by the generic O(R^2) DFT (sec. 4.2.5,
+// eq. (1) in its conjugate-pair form): output q of butterfly j is
+//   y_q = x_0 + sum_{r=1}^{(R-1)/2} [c (x_r + x_{R-r}) + i s (x_r - x_{R-r})],
+// w_R^{rq} = c + i s.  Each thread computes outputs idx = u + i*tpt (j = idx
+// div R, q = idx mod R) from the R inputs of its butterfly; L = 1 at stage 0,
+// so no twiddles and output idx lands at position j R + q = idx.
+__device__ __noinline__ void generic_stage(const Src& src, float2* xrow, const Dst* dst, int u, int tpt, int n,
+                                              int R, const float2* __restrict__ wp, bool valid) {
+  const int nb = n / R, h = (R - 1) / 2;
+  float2 y[16];
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int idx = u + i * tpt;
+      if (idx < n) {
+        const int j = idx / R, q = idx - (idx / R) * R;
+        auto ld = [&](int e) {
+          float2 x = src.padded ? src.p[physm(e)] : src.p[e * src.stride];
+          if (src.conj) x.y = -x.y;
+          return x;
+        };
+        float2 acc = ld(j);
+        int m = 0;
+        for (int r = 1; r <= h; ++r) {
+          m += q;
+          if (m >= R) m -= R;
+          const float2 a = ld(j + r * nb), b = ld(j + (R - r) * nb);
+          const float2 w = __ldg(wp + m);
+          const float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
+          acc.x = fmaf(w.x, sx, fmaf(-w.y, dy, acc.x));
+          acc.y = fmaf(w.x, sy, fmaf(w.y, dx, acc.y));
+        }
+        y[i] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int idx = u + i * tpt;
+      if (idx < n) {
+        if (dst) store_g(*dst, idx, y[i]);
+        else xrow[physm(idx)] = y[i];
+      }
+    }
+  }
+}
 
 template <int R, bool UNIT>
 __device__ __forceinline__ void stage_out_g(const float2* v, const Dst& d, int u, int tpt, int nb, int L,
@@ -331,8 +393,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     const bool last0 = k.nst == 1;
     const bool ok0 = v0 && t0 < cnt;
     // one stage: the host builds this only when the load and store mappings agree
-    any_stage(k.radix[0], v, s0, xbuf + t0 * k.pitch, last0 ? &dst : nullptr, u0, tpt, n, k.L[0], k.Lmagic[0],
-              nullptr, ok0, true);
+    if (k.radix[0] > 16)
+      generic_stage(s0, xbuf + t0 * k.pitch, last0 ? &dst : nullptr, u0, tpt, n, k.radix[0], k.wp, ok0);
+    else
+      any_stage(k.radix[0], v, s0, xbuf + t0 * k.pitch, last0 ? &dst : nullptr, u0, tpt, n, k.L[0], k.Lmagic[0],
+                nullptr, ok0, true);
     // the landing buffer is free: refill it with the tile two ahead
     if (tma && tid == 0) {
       const int64_t next = tile + 2 * (int64_t)gridDim.x;
@@ -426,9 +491,8 @@ int gb_mr_threads(int n, const int* radix, int nst) {
   int tpt = 1;
   for (int s = 0; s < nst; ++s) {
     const int R = radix[s];
-    const int bmax = 16 / R;
-    const int nb = n / R;
-    const int need = (nb + bmax - 1) / bmax;
+    // at most 16 values per thread; the generic prime stage: 16 outputs
+    const int need = R > 16 ? (n + 15) / 16 : (n / R + 16 / R - 1) / (16 / R);
     if (need > tpt) tpt = need;
   }
   return tpt;

@@ -360,3 +360,44 @@ def test_transpose_first_plans(n, b):
     for is_ in (b, b + 3):  # dense and padded input rows
         err, info = check([(n, is_, 1)], [(b, 1, n)], -1, x, flags=EST, algo="ct")
         assert "transpose first" in info, info
+
+
+# ---------------------------------------------------------------- generic prime stage
+
+@pytest.mark.parametrize("n", [17, 19, 23, 61, 68, 177, 345, 3904, 4070, 4880])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_generic_prime_stage(n, sign):
+    """One prime factor 17..61 (the generic O(p^2) DFT in conjugate-pair form,
+    sec. 4.2.5) as the first stage of the mixed-radix kernel."""
+    b = max(3, 30000 // n)
+    x = u(n * b, 950 + n)
+    err, info = check([(n, 1, 1)], [(b, n, n)], sign, x, flags=EST, algo="direct" if n <= 4096 else "ct")
+    assert "pass mr-tma" in info and "R=" in info, info
+
+
+def test_generic_prime_strided_and_group():
+    """Strided columns with a generic prime radix; a group with such a plan
+    (no generic one-CTA form) uses the graph of plan launches."""
+    n, cols = 61 * 8, 32
+    x = u(n * cols, 960)
+    err, info = check([(n, cols, 1)], [(cols, 1, n)], 1, x, flags=EST)
+    assert "pass mr-tma n=488 R=61.8 load=rows" in info, info
+    p = gbfft.Plan([(59, 1, 1)], [(40, 59, 59)], -1, EST)
+    q = gbfft.Plan([(4096, 1, 1)], [(4, 4096, 4096)], -1, EST)
+    try:
+        g = gbfft.fft_group_create([p.handle, q.handle])
+        assert gbfft.fft_group_mode(g) == 2
+        with pytest.raises(gbfft.GbfftError):
+            gbfft.fft_group_create([p.handle, q.handle], gbfft.FFT_GROUP_PERSISTENT)
+        xa = torch.from_numpy(u(59 * 40, 961)).cuda()
+        xb = torch.from_numpy(u(4096 * 4, 962)).cuda()
+        ya, yb = torch.zeros_like(xa), torch.zeros_like(xb)
+        gbfft.fft_group_execute(g, [xa.data_ptr(), xb.data_ptr()], [ya.data_ptr(), yb.data_ptr()],
+                                torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        gbfft.fft_group_destroy(g)
+        ref = reference([(59, 1, 1)], [(40, 59, 59)], -1, xa.cpu().numpy())
+        assert per_transform_error(ya.cpu().numpy(), ref, [(59, 1, 1)], [(40, 59, 59)]).max() <= TOL
+    finally:
+        p.destroy()
+        q.destroy()
