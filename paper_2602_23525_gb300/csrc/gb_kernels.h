@@ -33,6 +33,10 @@ struct GbP2 {
   int64_t grid;        // <= 0: persistent grid sized by occupancy
 };
 int gb_p2_supported(int logn, int load, int store, int posttw);
+// tensor map (128 bytes at map, 64-byte aligned) of the LOAD_ROWS tiles of k
+// with T columns: dims (V0, n, vector loops by stride), box (T, min(n, 256));
+// returns 0 when the layout has none; swap = 1 when the loops are (nb2, nb1)
+int gb_p2_rows_map(const GbP2& k, int T, void* map, int* swap);
 // cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
 // query, so the library needs no link-time libcuda); nullptr if unavailable
 void* gb_tensor_map_encoder(void);

@@ -427,6 +427,14 @@ void* gb_tensor_map_encoder() {
   return reinterpret_cast<void*>(fn);
 }
 
+int gb_p2_rows_map(const GbP2& k, int T, void* map, int* swap) {
+  GbRowsMap rm;
+  make_rows_map(k, T, &rm);
+  memcpy(map, &rm.map, sizeof(CUtensorMap));
+  *swap = rm.swap;
+  return rm.use;
+}
+
 int gb_p2_supported(int logn, int load, int store, int posttw) {
   const bool cc = load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG;
   if (cc) return !posttw && logn >= 4 && logn <= 13;

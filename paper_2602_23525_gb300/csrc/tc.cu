@@ -1,28 +1,38 @@
-// tc.cu -- radix-16 Stockham stages on the tensor cores (sm_103a).
+// tc.cu -- radix-16 Stockham stages on the 5th-generation tensor cores
+// (tcgen05, sm_103a).
 //
-// A radix-16 stage applies the 16-point DFT matrix F (F[s][r] = w_16^{r s},
-// eq. (1)) to every butterfly after the stage twiddles.  Here a warp takes 16
-// butterflies at a time as the rows of X (16 x 16, butterfly x point) and
-// computes Y = X F^T with mma.sync.m16n8k16 (two output halves of 8), complex
-// arithmetic as four real products:
-//   Y_re = X_re F_re^T + X_im (-F_im)^T,   Y_im = X_re F_im^T + X_im F_re^T,
-// operands rounded to FP16 or BF16, accumulation in FP32.  Twiddles are
-// applied in FP32 before the rounding (table of (w, w^2, w^4, w^8), as in
-// the FP32 kernels).  The split variants write every operand as hi + lo
-// (hi = round(v), lo = round(v - hi)) and accumulate
-// hi*hi + hi*lo + lo*hi, recovering about twice the operand precision.
-// With F as the B operand, the output columns a thread holds are the same
-// point indices as the input columns it loaded, so each butterfly's data
-// stays with the same four lanes from load to store.
+// A radix-16 stage applies the 16-point DFT matrix F (F[q][r] = w_16^{r q},
+// eq. (1)) to every butterfly after the stage twiddles.  A tile holds 256
+// butterflies (4096 points), one per thread; the stage is the real product
+//   [Y_re | Y_im] = [X_re | X_im] . [[F_re, F_im], [-F_im, F_re]]
+// of a 256 x 32 operand A (butterflies x points, re then im, rounded to FP16
+// or BF16) with the constant 32 x 32 operand B, accumulated in FP32 in tensor
+// memory: two tcgen05.mma of M = 128, N = 32 (K = 32 in two steps of 16),
+// issued by one thread, completion signalled on an mbarrier through
+// tcgen05.commit.  Each thread writes its butterfly as row `tid` of A in
+// shared memory (the canonical K-major layout of 8 x 16-byte core matrices,
+// no swizzle) and reads row `tid` of the result -- TMEM lane tid mod 128 in
+// the column block of M-tile tid / 128 -- with tcgen05.ld.  Twiddles are
+// applied in FP32 before the rounding (table of (w, w^2, w^4, w^8), as in the
+// FP32 kernels).  The split forms write every operand as hi + lo (hi =
+// round(v), lo = round(v - hi)) and accumulate hi*hi + lo*hi + hi*lo:
+// [A_hi | A_lo] . [B_hi ; B_hi] (K = 64) then A_hi . B_lo (K = 32).
 //
-// Tiles move as in stockham_pow2.cu: TMA bulk copies double-buffered on
-// mbarriers (bounded waits) into a persistent CTA, contiguous transforms
-// (LOAD_CONTIG) or T adjacent columns (LOAD_ROWS), stores contiguous or
-// column-wise.  Sizes: 2^8 and 2^12 points (all stages radix 16).
+// Tiles move as in stockham_pow2.cu: copy-engine loads (bulk copies of
+// contiguous transforms, tensor-map boxes of T columns) on an mbarrier into
+// one landing buffer per persistent CTA, refilled as soon as stage 0 has read
+// it; two CTAs per SM hide each other's copy and MMA waits.  Stores are
+// contiguous or column-wise.  Sizes:
+// 2^8 and 2^12 points (all stages radix 16).  Every wait is bounded by
+// %globaltimer; a CTA whose wait gives up records FFT_ERR_DEVICE_TIMEOUT and
+// leaves the tile loop, and always frees its tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cstring>
 
 #include "gb_kernels.h"
 #include "gb_tma.cuh"
@@ -47,13 +57,15 @@ struct TC {
   }
 };
 
-__device__ __forceinline__ int phys(int i) { return i + (i >> 5); }
+// operand precision: PREC 1/3 = FP16, 2/4 = BF16; 3/4 split into hi + lo
+template <int PREC>
+struct Prec {
+  static constexpr bool split = PREC >= 3;
+  static constexpr int KA = split ? 8 : 4;   // 8-element K chunks per row of A: [hi | lo] or [x]
+  static constexpr int KB = split ? 12 : 4;  // per row of B: [hi | hi | lo] or [F]
+  static constexpr uint32_t fmt = (PREC == 1 || PREC == 3) ? 0u : 1u;  // F16 0, BF16 1
+};
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// operand rounding: PREC 1/3 = FP16, 2/4 = BF16; 3/4 split into hi + lo
 template <int PREC>
 __device__ __forceinline__ uint32_t pack(float a, float b) {
   if constexpr (PREC == 1 || PREC == 3) {
@@ -76,7 +88,6 @@ __device__ __forceinline__ float2 unpack(uint32_t u) {
   }
 }
 
-// hi and lo words of the pair (a, b)
 template <int PREC>
 __device__ __forceinline__ void pack_split(float a, float b, uint32_t* hi, uint32_t* lo) {
   *hi = pack<PREC>(a, b);
@@ -84,198 +95,195 @@ __device__ __forceinline__ void pack_split(float a, float b, uint32_t* hi, uint3
   *lo = pack<PREC>(a - h.x, b - h.y);
 }
 
-template <int PREC>
-__device__ __forceinline__ void mma(float* d, const uint32_t* a, const uint32_t* b) {
-  if constexpr (PREC == 1 || PREC == 3) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-  } else {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-  }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// The DFT matrix as B operands (F^T, 16 x 8 per output half h): lane (g, t4)
-// holds rows 2t4, 2t4+1 (word 0) and 2t4+8, 2t4+9 (word 1) of column 8h+g.
-template <int PREC>
-struct FragF {
-  uint32_t re[2][2], im[2][2], nim[2][2];           // hi (or only) words
-  uint32_t re_l[2][2], im_l[2][2], nim_l[2][2];     // lo words (split)
-  __device__ void init(int g, int t4) {
-    constexpr bool split = PREC >= 3;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int s = 8 * h + g;
-#pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        const int r0 = 2 * t4 + 8 * w, r1 = r0 + 1;
-        const int m0 = (r0 * s) & 15, m1 = (r1 * s) & 15;
-        if (split) {
-          pack_split<PREC>(C16[m0], C16[m1], &re[h][w], &re_l[h][w]);
-          pack_split<PREC>(S16[m0], S16[m1], &im[h][w], &im_l[h][w]);
-          pack_split<PREC>(-S16[m0], -S16[m1], &nim[h][w], &nim_l[h][w]);
-        } else {
-          re[h][w] = pack<PREC>(C16[m0], C16[m1]);
-          im[h][w] = pack<PREC>(S16[m0], S16[m1]);
-          nim[h][w] = pack<PREC>(-S16[m0], -S16[m1]);
-        }
-      }
-    }
-  }
-};
+__device__ __forceinline__ int phys(int i) { return i + (i >> 5); }
 
-// w^e for e in {2t4, 2t4+1, 2t4+8, 2t4+9} from the (w, w^2, w^4, w^8) table entry
-__device__ __forceinline__ void lane_powers(const float4* tw, int t4, float2* p) {
+// byte offset of the 16-byte row piece (row, K chunk c) in the canonical
+// K-major layout without swizzle: core matrices of 8 rows x 16 bytes, K
+// chunks adjacent (leading byte offset 128), 8-row groups KC*128 apart
+__device__ __forceinline__ uint32_t core_off(int row, int c, int KC) {
+  return (uint32_t)(((row >> 3) * KC + c) * 128 + (row & 7) * 16);
+}
+
+// shared-memory matrix descriptor (start >> 4, LBO >> 4, SBO >> 4, version 1,
+// no swizzle)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// the powers w^1..w^15 from (w, w^2, w^4, w^8), at most three products each
+__device__ __forceinline__ void twiddle16(float2* v, const float4* tw) {
   const float4 a = __ldg(tw), b = __ldg(tw + 1);
-  const float2 w1 = make_float2(a.x, a.y), w2 = make_float2(a.z, a.w);
-  const float2 w4 = make_float2(b.x, b.y), w8 = make_float2(b.z, b.w);
-  float2 e = make_float2(1.f, 0.f);
-  if (t4 & 1) e = w2;
-  if (t4 & 2) e = cmul(e, w4);
-  p[0] = e;
-  p[1] = cmul(e, w1);
-  p[2] = cmul(e, w8);
-  p[3] = cmul(p[1], w8);
+  float2 p[16];
+  p[1] = make_float2(a.x, a.y);
+  p[2] = make_float2(a.z, a.w);
+  p[4] = make_float2(b.x, b.y);
+  p[8] = make_float2(b.z, b.w);
+  p[3] = cmul(p[2], p[1]);
+  p[5] = cmul(p[4], p[1]);
+  p[6] = cmul(p[4], p[2]);
+  p[7] = cmul(p[4], p[3]);
+#pragma unroll
+  for (int r = 9; r < 16; ++r) p[r] = cmul(p[8], p[r - 8]);
+#pragma unroll
+  for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], p[r]);
 }
 
-// One tensor-core radix-16 stage for the 256 butterflies of a tile (8 warps x
-// 32).  Loads + twiddles + MMAs happen before the caller's barrier (via
-// stage_mma), the stores after it (stage_store).
-template <int LOGN, int PREC>
-struct Stage {
-  float yre[2][2][4], yim[2][2][4];  // [group][output half][fragment]
+// row `row` of A: points 0..15 re (chunks 0, 1), im (chunks 2, 3); split:
+// hi (0..3), lo (4..7)
+template <int PREC>
+__device__ __forceinline__ void write_row(uint32_t abase, int row, const float2* x) {
+  using P = Prec<PREC>;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int r0 = (c & 1) * 8;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float a = (c < 2) ? x[r0 + 2 * i].x : x[r0 + 2 * i].y;
+      const float b = (c < 2) ? x[r0 + 2 * i + 1].x : x[r0 + 2 * i + 1].y;
+      if constexpr (P::split) pack_split<PREC>(a, b, &h[i], &l[i]);
+      else h[i] = pack<PREC>(a, b);
+    }
+    st_shared_v4(abase + core_off(row, c, P::KA), h[0], h[1], h[2], h[3]);
+    if constexpr (P::split) st_shared_v4(abase + core_off(row, 4 + c, P::KA), l[0], l[1], l[2], l[3]);
+  }
+}
 
-  // src(t, e) gives the address of element e of tile transform t
-  template <int S, typename Src>
-  __device__ __forceinline__ void load_mma(const Src& src, const float2* __restrict__ twt, const FragF<PREC>& F,
-                                           int w, int g, int t4, int conj) {
-    using C = TC<LOGN>;
-    constexpr int L = C::L(S);
-    constexpr bool split = PREC >= 3;
+// B^T (rows n = output re 0..15 then im 0..15, K = points re then im):
+// n < 16:  [C(nr) | -S(nr)],  n >= 16: [S(qr) | C(qr)] with q = n - 16;
+// split: [hi | hi | lo]
+template <int PREC>
+__device__ void build_b(uint32_t bbase, int tid) {
+  using P = Prec<PREC>;
+  if (tid >= 32) return;
+  const int n = tid, q = n & 15;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      float2 x[2][4];  // [row: g, g+8][point: 2t4, 2t4+1, 2t4+8, 2t4+9]
+  for (int c = 0; c < 4; ++c) {
+    uint32_t h[4], l[4];
 #pragma unroll
-      for (int hr = 0; hr < 2; ++hr) {
-        const int G = 32 * w + 16 * q + g + 8 * hr;
-        const int t = G / C::NBF, j = G % C::NBF;
+    for (int i = 0; i < 4; ++i) {
+      float v2[2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int r = 2 * t4 + (i & 1) + 8 * (i >> 1);
-          float2 v = src(t, j + r * C::NBF);
-          if (S == 0 && conj) v.y = -v.y;
-          x[hr][i] = v;
-        }
-        if constexpr (L > 1) {
-          float2 p[4];
-          lane_powers(reinterpret_cast<const float4*>(twt + C::twoff(S) + (j & (L - 1)) * 4), t4, p);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) x[hr][i] = cmul(x[hr][i], p[i]);
-        }
+      for (int e = 0; e < 2; ++e) {
+        const int k = c * 8 + 2 * i + e;  // 0..31
+        const int r = k & 15, m = (q * r) & 15;
+        const bool kim = k >= 16;
+        v2[e] = n < 16 ? (kim ? -S16[m] : C16[m]) : (kim ? C16[m] : S16[m]);
       }
-      // A fragments: word 0 = row g points (2t4, 2t4+1), word 1 = row g+8, words 2/3 = points +8
-      uint32_t ar[4], ai[4], arl[4], ail[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int hr = k & 1, i0 = (k >> 1) * 2;
-        if (split) {
-          pack_split<PREC>(x[hr][i0].x, x[hr][i0 + 1].x, &ar[k], &arl[k]);
-          pack_split<PREC>(x[hr][i0].y, x[hr][i0 + 1].y, &ai[k], &ail[k]);
-        } else {
-          ar[k] = pack<PREC>(x[hr][i0].x, x[hr][i0 + 1].x);
-          ai[k] = pack<PREC>(x[hr][i0].y, x[hr][i0 + 1].y);
-        }
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float* dr = yre[q][h];
-        float* di = yim[q][h];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) dr[i] = di[i] = 0.f;
-        mma<PREC>(dr, ar, F.re[h]);
-        mma<PREC>(dr, ai, F.nim[h]);
-        mma<PREC>(di, ar, F.im[h]);
-        mma<PREC>(di, ai, F.re[h]);
-        if (split) {
-          mma<PREC>(dr, arl, F.re[h]);
-          mma<PREC>(dr, ar, F.re_l[h]);
-          mma<PREC>(dr, ail, F.nim[h]);
-          mma<PREC>(dr, ai, F.nim_l[h]);
-          mma<PREC>(di, arl, F.im[h]);
-          mma<PREC>(di, ar, F.im_l[h]);
-          mma<PREC>(di, ail, F.re[h]);
-          mma<PREC>(di, ai, F.re_l[h]);
-        }
-      }
+      if constexpr (P::split) pack_split<PREC>(v2[0], v2[1], &h[i], &l[i]);
+      else h[i] = pack<PREC>(v2[0], v2[1]);
+    }
+    st_shared_v4(bbase + core_off(n, c, P::KB), h[0], h[1], h[2], h[3]);
+    if constexpr (P::split) {
+      st_shared_v4(bbase + core_off(n, 4 + c, P::KB), h[0], h[1], h[2], h[3]);
+      st_shared_v4(bbase + core_off(n, 8 + c, P::KB), l[0], l[1], l[2], l[3]);
     }
   }
+}
 
-  // dst(t, idx) gives the address of output idx of tile transform t
-  template <int S, typename Dst>
-  __device__ __forceinline__ void store(const Dst& dst, int w, int g, int t4, int conj, bool last,
-                                        int64_t valid_T) {
-    using C = TC<LOGN>;
-    constexpr int L = C::L(S);
+// D (TMEM, 2 M-tiles x 32 columns) = A . B for the 256 rows of A; the split
+// forms run K steps over [A_hi | A_lo] . [B_hi ; B_hi] and then A_hi . B_lo
+template <int PREC>
+__device__ __forceinline__ void issue_mma(uint32_t tmem, uint32_t abase, uint32_t bbase, uint32_t bar) {
+  using P = Prec<PREC>;
+  constexpr uint32_t idesc = (1u << 4) | (P::fmt << 7) | (P::fmt << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+  constexpr int KSTEPS = P::KB / 2;  // 16 elements = 2 chunks per step
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+  for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int row = g + 8 * (f >> 1);
-          const int s = 8 * h + 2 * t4 + (f & 1);
-          const int G = 32 * w + 16 * q + row;
-          const int t = G / C::NBF, j = G % C::NBF;
-          const int k = j & (L - 1);
-          const int idx = (j - k) * 16 + k + s * L;
-          float2 v = make_float2(yre[q][h][f], yim[q][h][f]);
-          if (last) {
-            if (t >= valid_T) continue;
-            if (conj) v.y = -v.y;
-          }
-          *dst(t, idx) = v;
-        }
+    for (int s = 0; s < KSTEPS; ++s) {
+      const int sa = s < P::KA / 2 ? s : s - P::KA / 2;  // A chunks: steps past A's end reuse A_hi
+      const uint64_t ad = smem_desc(abase + (uint32_t)(mt * 16 * P::KA * 128 + sa * 256), 128, P::KA * 128);
+      const uint64_t bd = smem_desc(bbase + (uint32_t)(s * 256), 128, P::KB * 128);
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(32 * mt)),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(s) : "memory");
+    }
   }
-};
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// row `tid` of D: 32 FP32 columns = Y_re[0..15], Y_im[0..15]
+__device__ __forceinline__ void read_row(uint32_t tmem, int tid, float2* y) {
+  const int w = tid >> 5;
+  const uint32_t ta = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(32 * (w >> 2));
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) y[q] = make_float2(__uint_as_float(r[q]), __uint_as_float(r[16 + q]));
+}
 
 template <int LOGN, int PREC, int LOAD, int STORE>
-__global__ void __launch_bounds__(256, 1) gb_tc_kernel(const __grid_constant__ GbP2 k) {
+__global__ void __launch_bounds__(256, 2) gb_tc_kernel(const __grid_constant__ GbP2 k,
+                                                       const __grid_constant__ CUtensorMap tm, int tmap, int swap) {
   using C = TC<LOGN>;
+  using P = Prec<PREC>;
   constexpr int T = (LOAD == GB_P2_LOAD_CONTIG && STORE == GB_P2_STORE_CONTIG) ? 4096 / C::N : 16;
   static_assert(T * C::NBF == 256, "a tile is 256 butterflies");
   constexpr int TILE = T * C::N;
-  constexpr int NBUF = 2;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-  float2* ibuf = reinterpret_cast<float2*>(smem_raw + 128);
+  constexpr int NBUF = 1;  // one landing buffer: two CTAs per SM overlap each other's waits
+  constexpr uint32_t ABYTES = 256 * P::KA * 16, BBYTES = 32 * P::KB * 16;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);  // [0, NBUF) tiles, [NBUF] mma
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + 64);
+  const uint32_t abase = smem_addr(smem_raw + 1024);
+  const uint32_t bbase = abase + ABYTES;
+  float2* ibuf = reinterpret_cast<float2*>(smem_raw + 1024 + ABYTES + BBYTES);
   float2* xbuf = ibuf + NBUF * TILE;
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
-  FragF<PREC> F;
-  F.init(g, t4);
-  const int64_t cblocks = (k.V0 + T - 1) / T;
-  const int64_t ntiles = cblocks * k.nb1 * k.nb2;
+  const int tid = threadIdx.x, lane = tid & 31;
+  // butterfly of this thread: lanes across the transforms for column tiles
+  constexpr bool TFAST = LOAD == GB_P2_LOAD_ROWS;
+  const int bt = TFAST ? tid % T : tid / C::NBF, bj = TFAST ? tid / T : tid % C::NBF;
+
   if (tid == 0) {
-    for (int b = 0; b < NBUF; ++b)
+    for (int b = 0; b < NBUF + 1; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  build_b<PREC>(bbase, tid);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  auto origin = [&](int64_t tile, int64_t* ib, int64_t* ob, int64_t* c0) {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t mbar = smem_addr(bars + NBUF);
+
+  const int64_t cblocks = (k.V0 + T - 1) / T;
+  const int64_t ntiles = cblocks * k.nb1 * k.nb2;
+  auto origin = [&](int64_t tile, int64_t* ib, int64_t* ob, int64_t* c0, int64_t* b1, int64_t* b2) {
     const int64_t cb = tile % cblocks, r = tile / cblocks;
-    const int64_t b1 = r % k.nb1, b2 = r / k.nb1;
+    *b1 = r % k.nb1;
+    *b2 = r / k.nb1;
     *c0 = cb * T;
-    *ib = b1 * k.vis1 + b2 * k.vis2 + *c0 * k.vis0;
-    *ob = b1 * k.vos1 + b2 * k.vos2 + *c0 * k.vos0;
+    *ib = *b1 * k.vis1 + *b2 * k.vis2 + *c0 * k.vis0;
+    *ob = *b1 * k.vos1 + *b2 * k.vos2 + *c0 * k.vos0;
   };
   auto issue = [&](int b, int64_t tile) {
-    int64_t ib, ob, c0;
-    origin(tile, &ib, &ob, &c0);
+    int64_t ib, ob, c0, b1, b2;
+    origin(tile, &ib, &ob, &c0, &b1, &b2);
     const int64_t cnt = (k.V0 - c0) < T ? (k.V0 - c0) : T;
     const uint32_t bar = smem_addr(bars + b);
     float2* dst = ibuf + b * TILE;
@@ -291,8 +299,18 @@ __global__ void __launch_bounds__(256, 1) gb_tc_kernel(const __grid_constant__ G
     } else {
       if (lane == 0) expect_tx(bar, (uint32_t)(C::N * T * 8));
       __syncwarp();
-      for (int e = lane; e < C::N; e += 32)
-        bulk_copy(smem_addr(dst + e * T), k.in + ib + (int64_t)e * k.is, (uint32_t)(T * 8), bar);
+      if (tmap) {
+        if (lane == 0) {
+          constexpr int BOXR = C::N < 256 ? C::N : 256;
+#pragma unroll
+          for (int r0 = 0; r0 < C::N; r0 += BOXR)
+            tensor_copy_4d(smem_addr(dst + r0 * T), &tm, (int)c0, r0, swap ? (int)b2 : (int)b1,
+                           swap ? (int)b1 : (int)b2, bar);
+        }
+      } else {
+        for (int e = lane; e < C::N; e += 32)
+          bulk_copy(smem_addr(dst + e * T), k.in + ib + (int64_t)e * k.is, (uint32_t)(T * 8), bar);
+      }
     }
   };
   if (tid < 32)
@@ -300,70 +318,118 @@ __global__ void __launch_bounds__(256, 1) gb_tc_kernel(const __grid_constant__ G
       const int64_t tile = blockIdx.x + (int64_t)b * gridDim.x;
       if (tile < ntiles) issue(b, tile);
     }
-  Stage<LOGN, PREC> st;
+
+  uint32_t mphase = 0;
+  bool bad = false;
   int it = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+  for (int64_t tile = blockIdx.x; tile < ntiles && !bad; tile += gridDim.x, ++it) {
     const int b = it % NBUF;
     const bool ok = mbar_wait(smem_addr(bars + b), (uint32_t)((it / NBUF) & 1));
     if (__syncthreads_or(!ok)) {
-      if (tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
-      return;
+      bad = true;
+      break;
     }
-    int64_t ib, ob, c0;
-    origin(tile, &ib, &ob, &c0);
+    int64_t ib, ob, c0, b1, b2;
+    origin(tile, &ib, &ob, &c0, &b1, &b2);
     const int64_t cnt = (k.V0 - c0) < T ? (k.V0 - c0) : T;
     const float2* tb = ibuf + b * TILE;
-    auto tile_src = [&](int t, int e) -> float2 {
-      return LOAD == GB_P2_LOAD_CONTIG ? tb[t * C::N + e] : tb[e * T + t];
-    };
-    auto x_src = [&](int t, int e) -> float2 { return xbuf[t * C::PITCH + phys(e)]; };
-    auto x_dst = [&](int t, int e) -> float2* { return xbuf + t * C::PITCH + phys(e); };
-    auto g_dst = [&](int t, int e) -> float2* {
-      return k.out + ob + (int64_t)t * k.vos0 + (STORE == GB_P2_STORE_COLS ? (int64_t)e * k.os : (int64_t)e);
-    };
-    st.template load_mma<0>(tile_src, k.twt, F, w, g, t4, k.conj);
-    __syncthreads();  // tile buffer read; previous tile's exchange reads done
-    if (tid < 32) {
-      const int64_t next = tile + (int64_t)NBUF * gridDim.x;
-      if (next < ntiles) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(b, next);
+#pragma unroll 1
+    for (int s = 0; s < C::NST; ++s) {
+      const int L = C::L(s);
+      float2 x[16];
+      // inputs of butterfly (bt, bj): elements bj + r*NBF
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int e = bj + r * C::NBF;
+        float2 v;
+        if (s == 0) {
+          v = LOAD == GB_P2_LOAD_CONTIG ? tb[bt * C::N + e] : tb[e * T + bt];
+          if (k.conj) v.y = -v.y;
+        } else {
+          v = xbuf[bt * C::PITCH + phys(e)];
+        }
+        x[r] = v;
       }
-    }
-    st.template store<0>(x_dst, w, g, t4, k.conj, false, T);
-    __syncthreads();
-    st.template load_mma<1>(x_src, k.twt, F, w, g, t4, k.conj);
-    if constexpr (C::NST == 2) {
-      st.template store<1>(g_dst, w, g, t4, k.conj, true, cnt);
-    } else {
-      __syncthreads();
-      st.template store<1>(x_dst, w, g, t4, k.conj, false, T);
-      __syncthreads();
-      st.template load_mma<2>(x_src, k.twt, F, w, g, t4, k.conj);
-      st.template store<2>(g_dst, w, g, t4, k.conj, true, cnt);
+      if (s > 0) twiddle16(x, reinterpret_cast<const float4*>(k.twt + C::twoff(s) + (bj & (L - 1)) * 4));
+      write_row<PREC>(abase, tid, x);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();  // A written, stage inputs read (tile or exchange rows), previous D read
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (s == 0 && tid < 32) {
+        // the landing buffer is free: refill it with the tile two ahead
+        const int64_t next = tile + (int64_t)NBUF * gridDim.x;
+        if (next < ntiles) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(b, next);
+        }
+      }
+      if (tid == 0) issue_mma<PREC>(tmem, abase, bbase, mbar);
+      const bool done = mbar_wait(mbar, mphase);
+      mphase ^= 1;
+      if (__syncthreads_or(!done)) {
+        bad = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float2 y[16];
+      read_row(tmem, tid, y);
+      // outputs q of butterfly bj land at (bj - kk)*16 + kk + q*L
+      const int kk = bj & (L - 1);
+      const int base = (bj - kk) * 16 + kk;
+      if (s == C::NST - 1) {
+        if (bt < cnt) {
+          float2* g = k.out + ob + (int64_t)bt * k.vos0;
+          const int64_t os = STORE == GB_P2_STORE_COLS ? k.os : 1;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            float2 v = y[q];
+            if (k.conj) v.y = -v.y;
+            g[(int64_t)(base + q * L) * os] = v;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) xbuf[bt * C::PITCH + phys(base + q * L)] = y[q];
+      }
+      __syncthreads();  // exchange rows written before the next stage reads them
     }
   }
+  if (bad && tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 template <int LOGN, int PREC, int LOAD, int STORE>
 cudaError_t launch(const GbP2& k, cudaStream_t st) {
   using C = TC<LOGN>;
+  using P = Prec<PREC>;
   constexpr int T = (LOAD == GB_P2_LOAD_CONTIG && STORE == GB_P2_STORE_CONTIG) ? 4096 / C::N : 16;
-  const size_t smem = 128 + sizeof(float2) * (2 * (size_t)T * C::N + (size_t)T * C::PITCH);
+  const size_t smem = 1024 + (size_t)256 * P::KA * 16 + (size_t)32 * P::KB * 16 +
+                      sizeof(float2) * ((size_t)T * C::N + (size_t)T * C::PITCH);
   auto fn = gb_tc_kernel<LOGN, PREC, LOAD, STORE>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int per_sm = 0, dev = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
-  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = ((k.V0 + T - 1) / T) * k.nb1 * k.nb2;
-  int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  // CTAs per SM from the shared memory they need (1 KB reserved each); the
+  // occupancy query reports one for this kernel although two are resident.
+  // Registers (launch bound 2) and tensor memory (64 columns each) allow two.
+  int sm_bytes = 0;
+  cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int per_sm = (sm_bytes >= 2 * (int)(smem + 1024)) ? 2 : 1;
+  int64_t grid = (int64_t)sms * per_sm;
   if (k.grid > 0) grid = k.grid;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) return cudaSuccess;
-  fn<<<(unsigned)grid, 256, smem, st>>>(k);
+  alignas(128) CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  int swap = 0, tmap = 0;
+  if (LOAD == GB_P2_LOAD_ROWS) tmap = gb_p2_rows_map(k, T, &tm, &swap);
+  fn<<<(unsigned)grid, 256, smem, st>>>(k, tm, tmap, swap);
   return cudaGetLastError();
 }
 
