@@ -62,7 +62,6 @@ def test_mixed_requests_match_oracle_and_alone():
     stats = gbfft.fft_server_stats(server)
     gbfft.fft_server_destroy(server)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
-    assert stats["merged_requests"] > 0
     assert 0 < stats["budget_high_water_bytes"] <= 256 << 20
     assert stats["p99_latency_s"] >= stats["p50_latency_s"] > 0
     for t, shape, batch, sign, x, hin, hout in reqs:
@@ -97,3 +96,31 @@ def test_budget_admission_and_rejection():
     gbfft.fft_server_destroy(server)
     assert stats["budget_high_water_bytes"] <= budget
     assert stats["rejected"] == 1
+
+
+def test_requests_merge_behind_a_blocked_head():
+    """Admission keeps arrival order: a head request waiting for budget holds
+    back the requests behind it, and the waiting ones of the same shape and
+    sign are then merged into one launch."""
+    big_n, big_b = 65536, 32               # 16 MiB in, 16 MiB out (+ scratch)
+    server = gbfft.fft_server_create(64 << 20, 2)
+    bufs = []
+    for i in range(2):
+        x = fft_inputs.uniform_c64(big_n * big_b, 970 + i)
+        bufs.append(((big_n,), big_b, x, torch.from_numpy(x).pin_memory(), torch.zeros(big_n * big_b,
+                     dtype=torch.complex64).pin_memory()))
+    for i in range(8):
+        x = fft_inputs.uniform_c64(4096 * 2, 980 + i)
+        bufs.append(((4096,), 2, x, torch.from_numpy(x).pin_memory(), torch.zeros(8192, dtype=torch.complex64).pin_memory()))
+    tickets = [gbfft.fft_server_submit(server, shape, b, -1, hin.data_ptr(), hout.data_ptr())
+               for shape, b, _, hin, hout in bufs]
+    assert gbfft.fft_server_drain(server, 120.0) == gbfft.FFT_OK
+    stats = gbfft.fft_server_stats(server)
+    gbfft.fft_server_destroy(server)
+    assert stats["completed"] == len(bufs) and stats["failed"] == 0
+    assert stats["merged_requests"] > 0, stats
+    assert stats["budget_high_water_bytes"] <= 64 << 20
+    for (shape, b, x, hin, hout) in bufs:
+        n = shape[0]
+        ref = reference([(n, 1, 1)], [(b, n, n)], -1, x)
+        assert per_transform_error(hout.numpy(), ref, [(n, 1, 1)], [(b, n, n)]).max() <= TOL
