@@ -296,9 +296,37 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, dev)
         nbytes = sum(8 * npts * count for _, _, _, npts, count in plans)
+        # the host link's own ceiling: one host -> device and one device -> host
+        # copy of the largest problem running at the same time on the two lanes
+        mmax = max(npts * count for _, _, _, npts, count in plans)
+        link_ms = []
+        for rep in range(4):
+            torch.cuda.synchronize()
+            c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c.record(stream)
+            for ls in lanes:
+                ls.wait_event(c)
+            with torch.cuda.stream(lanes[0]):
+                dbuf[0][0][:mmax].copy_(host_in[:mmax], non_blocking=True)
+            with torch.cuda.stream(lanes[1]):
+                host_out[1][:mmax].copy_(dbuf[1][1][:mmax], non_blocking=True)
+            for ls in lanes:
+                join = torch.cuda.Event()
+                join.record(ls)
+                stream.wait_event(join)
+            d.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                link_ms.append(c.elapsed_time(d))
+        link_gbs = 2 * 8 * mmax / (min(link_ms) * 1e-3) / 1e9
+        e2e_gbs = 2 * nbytes / (e2e_ms * 1e-3) / 1e9
         e2e = {"value": round(aggregate_gflops(world, step_flops, e2e_ms), 2), "unit": "GFLOP/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": round(e2e_ms, 3),
-               "pipeline": "two streams, copies of one problem overlap the transform of the other"}
+               "pipeline": "two streams, copies of one problem overlap the transform of the other",
+               "host_link": {"achieved_gbs": round(e2e_gbs, 1), "peak_gbs": round(link_gbs, 1),
+                             "frac": round(e2e_gbs / link_gbs, 3),
+                             "peak_kind": "measured here: concurrent pinned H2D + D2H copies of %d bytes each "
+                                          "on two streams" % (8 * mmax)}}
 
     launches = sum(p.launches for _, _, p, _, _ in plans) * args.steps
     result = {

@@ -754,17 +754,19 @@ struct Builder {
     float2* w = (float2*)dalloc(sizeof(float2) * n);
     float2* B = (float2*)dalloc(sizeof(float2) * m);
     if (device && !err) {
+      // FP64 work of the chirp's transform: stream-ordered allocation, since
+      // a plain cudaFree would wait for every stream of the device (a plan
+      // made while other transforms run would stall them)
       double2* work = nullptr;
-      if (cudaMalloc(&work, sizeof(double2) * 2 * m) != cudaSuccess) {
+      if (cudaMallocAsync((void**)&work, sizeof(double2) * 2 * m, 0) != cudaSuccess) {
         cudaGetLastError();
         err = FFT_ERR_OOM;
         return;
       }
       if (gb_make_chirp(w, n, 0) != cudaSuccess ||
-          gb_make_bluestein_kernel(B, n, m, rad.data(), (int)rad.size(), work, 0) != cudaSuccess ||
-          cudaStreamSynchronize(0) != cudaSuccess)
+          gb_make_bluestein_kernel(B, n, m, rad.data(), (int)rad.size(), work, 0) != cudaSuccess)
         err = FFT_ERR_CUDA;
-      cudaFree(work);
+      if (cudaFreeAsync(work, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) err = FFT_ERR_CUDA;
     }
     std::vector<Dim> VV = V;
     if (VV.empty()) VV.push_back({1, 0, 0});

@@ -11,8 +11,13 @@
 //     a free slot, so requests that arrive while others run are admitted as
 //     memory and slots free up, and their copies and transforms overlap on the
 //     device across the streams;
-//   * launch: host->device copies of each request's input, one plan execution
-//     of the merged batch, device->host copies of each output, an event.
+//   * launch: a three-stage pipeline over streams joined by events: the
+//     host->device copies of each request's input on the copy-in stream (one
+//     queue in admission order), the plan execution of the merged batch on the
+//     least busy compute stream, the device->host copies of each output on the
+//     copy-out stream (one queue); so both directions of the host link stay
+//     busy while transforms run, and a launch's copies never wait behind
+//     another launch's transform on the same stream.
 // Plans stay resident in a cache keyed by (shape, sign, batch bucket); they
 // use external scratch, so one plan serves launches on several streams.
 // A merged batch is padded up to its bucket (power of two); the padding
@@ -108,6 +113,7 @@ struct Request {
   const void* hin = nullptr;
   void* hout = nullptr;
   int64_t points = 0;  // per transform
+  std::string key;     // rank, extents and sign (requests that may merge)
   double arrival = 0, done = 0;
   int state = 0;       // 0 waiting, 1 running, 2 done, 3 failed
   int status = FFT_OK;
@@ -116,7 +122,8 @@ struct Request {
 struct Launch {
   std::vector<Request*> reqs;
   int stream = 0;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_fft = nullptr;  // inputs copied; transform done
+  cudaEvent_t ev = nullptr;                        // outputs copied (completion)
   size_t off = 0, bytes = 0;
 };
 
@@ -137,8 +144,9 @@ int64_t bucket_of(int64_t b) {
 struct fft_server_s {
   size_t budget = 0;
   int nstreams = 1;
-  int depth = 2;  // launches in flight per stream
-  std::vector<cudaStream_t> streams;
+  int depth = 4;  // launches in flight per compute stream
+  std::vector<cudaStream_t> streams;  // compute streams
+  cudaStream_t cin = nullptr, cout = nullptr;  // copy-in and copy-out queues
   std::vector<int> busy;
   Pool pool;
   std::mutex mu;
@@ -159,10 +167,13 @@ struct fft_server_s {
   size_t hwm = 0, in_use = 0;
   double first_arrival = -1, last_done = 0;
   int device = 0;
+  // why the head of the queue last waited: 0 not waiting, 1 stream slots, 2 memory
+  int blocked = 0;
+  double stall_slots = 0, stall_memory = 0;  // seconds the queue head waited, by reason
 
   fft_plan get_plan(const Request& r, int64_t bucket, int* err) {
     std::ostringstream k;
-    k << shape_key(r) << ":" << bucket;
+    k << r.key << ":" << bucket;
     auto it = plans.find(k.str());
     if (it != plans.end()) return it->second;
     fft_iodim d[3], h;
@@ -193,10 +204,12 @@ struct fft_server_s {
       }
       const double t = now_s() - t0;
       for (Request* r : L->reqs) {
-        r->state = q == cudaSuccess ? 2 : 3;
-        r->status = q == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
+        // a launch step that failed at submission keeps its code
+        const bool ok = q == cudaSuccess && r->status == FFT_OK;
+        r->state = ok ? 2 : 3;
+        if (q != cudaSuccess && r->status == FFT_OK) r->status = FFT_ERR_CUDA;
         r->done = t;
-        if (q == cudaSuccess) {
+        if (ok) {
           ++n_done;
           lat.push_back(r->done - r->arrival);
           flops += 5.0 * r->points * std::log2((double)std::max<int64_t>(2, r->points)) * r->batch;
@@ -210,7 +223,8 @@ struct fft_server_s {
       pool.release(L->off, L->bytes);
       in_use -= (L->bytes + 255) & ~(size_t)255;
       busy[L->stream]--;
-      cudaEventDestroy(L->ev);
+      for (cudaEvent_t e : {L->ev_in, L->ev_fft, L->ev})
+        if (e) cudaEventDestroy(e);
       delete L;
       inflight.erase(inflight.begin() + i);
       cv_done.notify_all();
@@ -220,19 +234,23 @@ struct fft_server_s {
   // admit as many launches as budget and stream slots allow; returns the count
   int admit_locked() {
     int admitted = 0;
+    blocked = 0;
     while (!waiting.empty()) {
       int s = -1;
       for (int i = 0; i < nstreams; ++i)
         if (busy[i] < depth && (s < 0 || busy[i] < busy[s])) s = i;
-      if (s < 0) break;
+      if (s < 0) {
+        blocked = 1;
+        break;
+      }
       Request* r = waiting.front();
-      const std::string key = shape_key(*r);
+      const std::string& key = r->key;
       // merge the waiting requests of the same shape and sign (arrival order kept)
       std::vector<Request*> group{r};
       int64_t total = r->batch;
       for (size_t i = 1; i < waiting.size() && i < 256; ++i) {
         Request* q = waiting[i];
-        if (shape_key(*q) == key && (total + q->batch) * r->points <= max_merge_points) {
+        if (q->key == key && (total + q->batch) * r->points <= max_merge_points) {
           group.push_back(q);
           total += q->batch;
         }
@@ -274,7 +292,10 @@ struct fft_server_s {
         continue;
       }
       size_t off = 0;
-      if (in_use + need > budget || !pool.alloc(need, &off)) break;  // wait for memory
+      if (in_use + need > budget || !pool.alloc(need, &off)) {  // wait for memory
+        blocked = 2;
+        break;
+      }
       in_use += (need + 255) & ~(size_t)255;
       hwm = std::max(hwm, in_use);
       Launch* L = new Launch;
@@ -287,22 +308,41 @@ struct fft_server_s {
       char* dscr = dout + ((data + 255) & ~(size_t)255);
       cudaStream_t st = streams[s];
       int rc = FFT_OK;
+      if (cudaEventCreateWithFlags(&L->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&L->ev_fft, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&L->ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = FFT_ERR_CUDA;
       size_t pos = 0;
       for (Request* q : group) {
         const size_t b = (size_t)q->batch * q->points * 8;
-        if (cudaMemcpyAsync(din + pos, q->hin, b, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = FFT_ERR_CUDA;
-        pos += b;
-      }
-      if (rc == FFT_OK) rc = fft_execute_scratch(p, din, dout, scratch ? dscr : nullptr, st);
-      pos = 0;
-      for (Request* q : group) {
-        const size_t b = (size_t)q->batch * q->points * 8;
-        if (rc == FFT_OK && cudaMemcpyAsync(q->hout, dout + pos, b, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        if (rc == FFT_OK && cudaMemcpyAsync(din + pos, q->hin, b, cudaMemcpyHostToDevice, cin) != cudaSuccess)
           rc = FFT_ERR_CUDA;
         pos += b;
       }
-      cudaEventCreateWithFlags(&L->ev, cudaEventDisableTiming);
-      cudaEventRecord(L->ev, st);
+      if (rc == FFT_OK && (cudaEventRecord(L->ev_in, cin) != cudaSuccess ||
+                           cudaStreamWaitEvent(st, L->ev_in, 0) != cudaSuccess))
+        rc = FFT_ERR_CUDA;
+      if (rc == FFT_OK) rc = fft_execute_scratch(p, din, dout, scratch ? dscr : nullptr, st);
+      if (rc == FFT_OK && (cudaEventRecord(L->ev_fft, st) != cudaSuccess ||
+                           cudaStreamWaitEvent(cout, L->ev_fft, 0) != cudaSuccess))
+        rc = FFT_ERR_CUDA;
+      pos = 0;
+      for (Request* q : group) {
+        const size_t b = (size_t)q->batch * q->points * 8;
+        if (rc == FFT_OK && cudaMemcpyAsync(q->hout, dout + pos, b, cudaMemcpyDeviceToHost, cout) != cudaSuccess)
+          rc = FFT_ERR_CUDA;
+        pos += b;
+      }
+      // completion: after the copy-out queue, and after every stream that may
+      // still touch the buffers when an earlier step failed
+      if (L->ev) {
+        if (rc != FFT_OK) {
+          cudaGetLastError();
+          if (L->ev_in && cudaEventRecord(L->ev_in, cin) == cudaSuccess) cudaStreamWaitEvent(cout, L->ev_in, 0);
+          if (L->ev_fft && cudaEventRecord(L->ev_fft, st) == cudaSuccess) cudaStreamWaitEvent(cout, L->ev_fft, 0);
+        }
+        cudaEventRecord(L->ev, cout);
+      }
       for (Request* q : group) {
         q->state = 1;
         if (rc != FFT_OK) q->status = rc;
@@ -325,13 +365,19 @@ struct fft_server_s {
   void loop() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
+    double last = now_s();
     while (true) {
       retire_locked();
       admit_locked();
       if (stop && waiting.empty() && inflight.empty()) break;
+      const int why = waiting.empty() ? 0 : blocked;
       lk.unlock();
       std::this_thread::sleep_for(std::chrono::microseconds(inflight.empty() && waiting.empty() ? 200 : 20));
       lk.lock();
+      const double t = now_s();
+      if (why == 1) stall_slots += t - last;
+      if (why == 2) stall_memory += t - last;
+      last = t;
     }
   }
 };
@@ -360,17 +406,23 @@ extern "C" fft_server fft_server_create(size_t budget_bytes, int nstreams, unsig
     set_err(FFT_ERR_OOM);
     return nullptr;
   }
-  for (int i = 0; i < nstreams; ++i) {
+  for (int i = 0; i < nstreams + 2; ++i) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+      if (s->cin) cudaStreamDestroy(s->cin);
       s->pool.destroy();
       delete s;
       set_err(FFT_ERR_CUDA);
       return nullptr;
     }
-    s->streams.push_back(st);
+    if (i < nstreams)
+      s->streams.push_back(st);
+    else if (!s->cin)
+      s->cin = st;
+    else
+      s->cout = st;
   }
   s->t0 = now_s();
   s->worker = std::thread([s] { s->loop(); });
@@ -399,6 +451,7 @@ extern "C" int fft_server_submit(fft_server s, int rank, const int64_t* n, int64
   }
   r->batch = batch;
   r->sign = sign;
+  r->key = shape_key(*r);
   r->hin = host_in;
   r->hout = host_out;
   std::lock_guard<std::mutex> g(s->mu);
@@ -475,7 +528,8 @@ extern "C" int fft_server_stats(fft_server s, char* buf, size_t len) {
       << ", \"gbs_algorithmic\": " << (span > 0 ? s->bytes_alg / span / 1e9 : 0.0)
       << ", \"requests_per_s\": " << (span > 0 ? s->n_done / span : 0.0) << ", \"budget_bytes\": " << s->budget
       << ", \"budget_high_water_bytes\": " << s->hwm << ", \"cached_plans\": " << s->plans.size()
-      << ", \"streams\": " << s->nstreams << "}";
+      << ", \"streams\": " << s->nstreams << ", \"stall_slots_s\": " << s->stall_slots
+      << ", \"stall_memory_s\": " << s->stall_memory << "}";
   }
   const std::string str = o.str();
   if (buf && len > 0) {
@@ -495,9 +549,13 @@ extern "C" void fft_server_destroy(fft_server s) {
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->device);
   for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
+  cudaStreamSynchronize(s->cin);
+  cudaStreamSynchronize(s->cout);
   for (auto& kv : s->plans) fft_destroy(kv.second);
   for (auto& kv : s->reqs) delete kv.second;
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  cudaStreamDestroy(s->cin);
+  cudaStreamDestroy(s->cout);
   s->pool.destroy();
   delete s;
 }
