@@ -48,6 +48,7 @@ static std::vector<Dim> canon_vec(std::vector<Dim> V) {
 
 struct PostTw {
   int64_t N;
+  int dim = 0;  // the column is the index along this vector dim (0: the tile dimension)
 };
 
 struct Builder {
@@ -286,6 +287,7 @@ struct Builder {
     p.conj = conj;
     if (tw) {
       p.post_tw = 1;
+      p.tw_dim = tw->dim;
       p.twN = tw->N;
       split_roots(tw->N, &p.tw_lo, &p.tw_hi, &p.twS);
     }
@@ -307,7 +309,7 @@ struct Builder {
     o << "pass stockham n=" << d.n << " is=" << d.is << " os=" << d.os << " cfg=" << cfg.str()
       << " tpt=" << p.tpt << " threads=" << s.threads << " smem=" << s.smem << " tiles=" << p.ntiles
       << " vdims=" << dims_str(V);
-    if (tw) o << " post-twiddle w_" << tw->N << "^(v0*k)";
+    if (tw) o << " post-twiddle w_" << tw->N << "^(v" << tw->dim << "*k)";
     if (conj) o << " conj";
     *out = s;
     *desc = o.str();
@@ -370,9 +372,12 @@ struct Builder {
     return true;
   }
 
-  void emit_p2(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t posttwN, int depth) {
+  // ptw_dim: the post-twiddle column is the index along the tile dimension (0)
+  // or along the pass's first / second other vector loop (1, 2; order_for_pass)
+  void emit_p2(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t posttwN, int depth,
+               int ptw_dim = 0) {
     P2Choice c;
-    if (!p2_choose(d, V, posttwN > 0, &c, prec)) {
+    if (!p2_choose(d, V, posttwN > 0, &c, prec) || (ptw_dim && (c.prec || ptw_dim > (int)c.rest.size()))) {
       err = FFT_ERR_WISDOM;
       return;
     }
@@ -399,6 +404,7 @@ struct Builder {
       k.vos2 = c.rest[1].os;
     }
     k.conj = conj;
+    k.ptw_dim = k.posttw ? ptw_dim : 0;
     k.status = P->d_status;
     float2* tw = (float2*)dalloc(sizeof(float2) * (size_t)std::max(16, gb_p2_twiddle_elems(c.logn)));
     for (int st = 1; tw && !err; ++st) {
@@ -409,9 +415,10 @@ struct Builder {
     k.twt = tw;
     if (k.posttw) {
       const int64_t L = gb_p2_last_L(c.logn);
-      float2* A = (float2*)dalloc(sizeof(float2) * (size_t)(k.V0 * L));
-      float2* B = (float2*)dalloc(sizeof(float2) * (size_t)(k.V0 * 4));
-      if (A && B && gb_make_posttw(A, B, posttwN, k.V0, L, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+      const int64_t ncols = ptw_dim ? c.rest[ptw_dim - 1].n : k.V0;
+      float2* A = (float2*)dalloc(sizeof(float2) * (size_t)(ncols * L));
+      float2* B = (float2*)dalloc(sizeof(float2) * (size_t)(ncols * 4));
+      if (A && B && gb_make_posttw(A, B, posttwN, ncols, L, 0) != cudaSuccess) err = FFT_ERR_CUDA;
       k.ptwA = A;
       k.ptwB = B;
     }
@@ -420,7 +427,7 @@ struct Builder {
     const std::vector<Dim> VV = order_for_pass(V);
     Dim v0{1, 0, 0};
     if (!VV.empty()) v0 = VV[0];
-    PostTw tw2{posttwN};
+    PostTw tw2{posttwN, ptw_dim};
     Step s;
     std::string desc;
     if (!make_single(d, VV, src, dst, conj, estimate_cfg(d, v0, !VV.empty(), default_radices(d.n)),
@@ -435,7 +442,9 @@ struct Builder {
     static const char* pn[] = {"p2-tma", "tc-fp16", "tc-bf16", "tc-fp16-split", "tc-bf16-split"};
     o << "pass " << pn[c.prec] << " n=" << d.n << " load=" << ln[c.load] << " store=" << sn[c.store] << " T=" << c.T
       << " is=" << d.is << " os=" << d.os << " tile=" << dims_str({c.v0}) << " rest=" << dims_str(c.rest)
-      << (k.posttw ? " post-twiddle w_" + std::to_string(posttwN) + "^(v0*k)" : std::string()) << (conj ? " conj" : "")
+      << (k.posttw ? " post-twiddle w_" + std::to_string(posttwN) + "^(v" + std::to_string(ptw_dim) + "*k)"
+                   : std::string())
+      << (conj ? " conj" : "")
       << " (fallback: " << desc << ")";
     line(depth, o.str());
   }
@@ -701,8 +710,62 @@ struct Builder {
     line(depth, o.str());
   }
 
+  static bool same_dim(const Dim& a, const Dim& b) { return a.n == b.n && a.is == b.is && a.os == b.os; }
+
+  // Four-step with the scratch layout [l2][k1][vector index] and one vector
+  // loop of unit input and output stride innermost (the transform runs down
+  // the columns of a row-major array: a rank-2/3 dimension other than the
+  // last, or a batch-fastest layout).  Both passes then tile along that loop
+  // (rows of adjacent columns in, rows out), and the pass-1 twiddle w_n^{l2 k1}
+  // takes its column l2 from a vector loop.  Returns false, emitting nothing,
+  // where the layout does not apply.
+  bool emit_fourstep_cols(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t n1,
+                          int depth) {
+    if (prec || d.is == 1 || V.empty() || V.size() > 2) return false;
+    int vs = -1;
+    for (int i = 0; i < (int)V.size(); ++i)
+      if (V[i].n > 1 && V[i].is == 1 && V[i].os == 1) vs = i;
+    if (vs < 0) return false;
+    const int64_t n = d.n, n2 = n / n1, count = prod_n(V);
+    // scratch strides: loop vs 1, the other loop next, k1 count, l2 n1 count
+    std::vector<Dim> Vs(V.size());
+    int64_t st = 1;
+    for (int i : {vs, 1 - vs}) {
+      if (i < 0 || i >= (int)V.size()) continue;
+      Vs[i] = {V[i].n, V[i].is, st};
+      st *= V[i].n;
+    }
+    const Dim l2{n2, d.is, n1 * count};
+    std::vector<Dim> V1{Vs[vs], l2};
+    if (V.size() == 2) V1.push_back(Vs[1 - vs]);
+    const Dim d1{n1, n2 * d.is, count};
+    const std::vector<Dim> O = order_for_pass(V1);
+    P2Choice pc;
+    if (!same_dim(O[0], Vs[vs]) || !p2_choose(d1, V1, true, &pc) || pc.load != GB_P2_LOAD_ROWS ||
+        pc.store != GB_P2_STORE_COLS)
+      return false;
+    int pos = -1;
+    for (int i = 1; i < (int)O.size(); ++i)
+      if (same_dim(O[i], l2)) pos = pos < 0 ? i : 99;  // unique match only
+    if (pos < 1 || pos > 2) return false;
+    std::ostringstream o;
+    o << "cooley-tukey n=" << n << " = " << n1 << " x " << n2 << " (radix-" << n1
+      << " step, eq. 2; columns innermost in the scratch)";
+    line(depth, o.str());
+    const int S = new_scratch((size_t)count * n * sizeof(float2));
+    // pass 1: n2 x count DFTs of size n1 over l1, twiddle w_n^{l2 k1}
+    emit_p2(d1, V1, src, S, conj, n, depth + 1, pos);
+    if (err) return true;
+    // pass 2: n1 x count DFTs of size n2 over l2, output Y[k1 + k2 n1]
+    std::vector<Dim> V2{{n1, count, d.os}, {V[vs].n, 1, V[vs].os}};
+    if (V.size() == 2) V2.push_back({V[1 - vs].n, Vs[1 - vs].os, V[1 - vs].os});
+    solve_rank1({n2, n1 * count, n1 * d.os}, V2, S, dst, conj, depth + 1);
+    return true;
+  }
+
   void emit_fourstep(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t n1,
                      int depth) {
+    if (emit_fourstep_cols(d, V, src, dst, conj, n1, depth)) return;
     const int64_t n = d.n, n2 = n / n1;
     std::ostringstream o;
     o << "cooley-tukey n=" << n << " = " << n1 << " x " << n2 << " (radix-" << n1 << " step, eq. 2)";
@@ -890,6 +953,15 @@ struct Builder {
     // strided tiles get thin)
     const bool xpose = !prec && xpose_ok(d, V);
     if (xpose && !measure && n >= 4096) c.push_back("xpose");
+    // estimate mode: transforms of 2^12 and more down the columns of a
+    // row-major array take the four-step with the columns innermost (two
+    // passes of 64-column tiles beat one pass of two-column tiles when measured)
+    if (!prec && !measure && d.is != 1 && log2_exact(n) >= 12) {
+      const int64_t a = estimate_split(n);
+      bool unit = false;
+      for (const Dim& v : V) unit = unit || (v.is == 1 && v.os == 1 && v.n % 64 == 0);
+      if (unit && a >= 64 && n / a >= 64) c.push_back("split:" + std::to_string(a));
+    }
     P2Choice pc;
     if (p2_choose(d, V, false, &pc, prec)) {
       c.push_back("p2");

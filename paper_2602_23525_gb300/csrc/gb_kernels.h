@@ -29,14 +29,17 @@ struct GbP2 {
   const float2* twt;   // per-stage [k][4] twiddle tables (gb_make_stage_twiddles)
   const float2* ptwA;  // post twiddle: A[c*L + j] = w_N^{c j}
   const float2* ptwB;  //               B[c] = (s, s^2, s^4, s^8), s = w_N^{c L}
+  int ptw_dim;         // the column c: 0 the index along the tile dimension, 1 along nb1, 2 along nb2
   int* status;
   int64_t grid;        // <= 0: persistent grid sized by occupancy
 };
 int gb_p2_supported(int logn, int load, int store, int posttw);
 // tensor map (128 bytes at map, 64-byte aligned) of the LOAD_ROWS tiles of k
-// with T columns: dims (V0, n, vector loops by stride), box (T, min(n, 256));
-// returns 0 when the layout has none; swap = 1 when the loops are (nb2, nb1)
-int gb_p2_rows_map(const GbP2& k, int T, void* map, int* swap);
+// with T columns: dims (V0, then the rows and the two vector loops ordered by
+// stride), box T x min(n, 256) rows; returns 0 when the layout has none;
+// *pos = the map dims (1..3) of the rows, nb1 and nb2, packed as
+// rows | nb1 << 2 | nb2 << 4
+int gb_p2_rows_map(const GbP2& k, int T, void* map, int* pos);
 // cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
 // query, so the library needs no link-time libcuda); nullptr if unavailable
 void* gb_tensor_map_encoder(void);

@@ -59,7 +59,8 @@ struct GbPass {
   // ---- sign ------------------------------------------------------------------
   int conj;             // 1: backward transform as conj(DFT_fwd(conj(x)))
   // ---- fused four-step twiddle ------------------------------------------------
-  int post_tw;          // multiply out[k] of transform v (vector dim 0) by w_N^{v k}
+  int post_tw;          // multiply out[k] of transform v by w_N^{c k}, c = its index along vector dim tw_dim
+  int tw_dim;           // 0: c = the tile dimension's index; 1, 2: another vector dim
   int64_t twN;          // N
   int64_t twS;          // w_N^m = hi[m / S] * lo[m % S]
   const float2* tw_lo;  // lo[i] = w_N^i,      i < S

@@ -63,6 +63,12 @@ __device__ __forceinline__ void tensor_copy_4d(uint32_t dst, const void* tmap, i
       : "memory");
 }
 
+// coordinate of tensor-map dim i (1..3) of a column tile whose rows, first and
+// second vector loop sit at the map dims packed in pos (rows | nb1 << 2 | nb2 << 4)
+__device__ __forceinline__ int map_coord(int pos, int i, int r0, int b1, int b2) {
+  return (pos & 3) == i ? r0 : (((pos >> 2) & 3) == i ? b1 : b2);
+}
+
 __device__ __forceinline__ void tensor_copy_3d(uint32_t dst, const void* tmap, int x, int y, int z, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "

@@ -66,6 +66,7 @@ struct TileCtx {
   bool tvalid;       // this thread's transform exists
   int64_t bin, bout; // element offsets of this thread's transform
   int64_t v0;        // its index along vector dim 0
+  int64_t col;       // post-twiddle column: its index along vector dim tw_dim
 };
 
 // One Stockham stage (see gb_pass.h).  from_g: stage 0 reads global memory;
@@ -112,7 +113,7 @@ __device__ __forceinline__ void stage(const GbPass& p, int s, float2* sm, const 
         for (int q = 0; q < R; ++q) {
           const int idx = base + q * L;
           float2 val = v[b][q];
-          if (p.post_tw) val = cmul(val, split_twiddle(p, c.v0 * (int64_t)idx));
+          if (p.post_tw) val = cmul(val, split_twiddle(p, c.col * (int64_t)idx));
           store_c(dst + (int64_t)idx * p.os, val, p.conj);
         }
       } else {
@@ -143,18 +144,21 @@ __device__ __forceinline__ void run_stage(const GbPass& p, int s, float2* sm, co
   }
 }
 
-// tile index -> base offsets of transform 0 of the tile and its dim-0 index
+// tile index -> base offsets of transform 0 of the tile, its dim-0 index and
+// its index along vector dim tw_dim (when that is not dim 0)
 __device__ __forceinline__ void tile_origin(const GbPass& p, int64_t tile, int64_t* bin,
-                                            int64_t* bout, int64_t* v0) {
+                                            int64_t* bout, int64_t* v0, int64_t* vtw) {
   int64_t rest = tile / p.tiles0;
   const int64_t i0 = (tile - rest * p.tiles0) * p.T;
   int64_t a = i0 * p.vis[0], b = i0 * p.vos[0];
+  *vtw = 0;
   for (int d = p.nv - 1; d >= 1; --d) {
     const int64_t q = rest / p.vn[d];
     const int64_t i = rest - q * p.vn[d];
     rest = q;
     a += i * p.vis[d];
     b += i * p.vos[d];
+    if (d == p.tw_dim) *vtw = i;
   }
   *bin = a;
   *bout = b;
@@ -182,14 +186,14 @@ __device__ void tile_load(const GbPass& p, const float2* in, float2* sm, int64_t
 }
 
 __device__ void tile_store(const GbPass& p, float2* out, const float2* sm, int64_t bout, int64_t v0,
-                           int ntv) {
+                           int64_t vtw, int ntv) {
   const int total = p.T * p.n;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int t, e;
     tile_index(p, idx, p.store_copy, &t, &e);
     if (t < ntv) {
       float2 val = sm[t * p.pitch + phys(e)];
-      if (p.post_tw) val = cmul(val, split_twiddle(p, (v0 + t) * (int64_t)e));
+      if (p.post_tw) val = cmul(val, split_twiddle(p, (p.tw_dim ? vtw : v0 + t) * (int64_t)e));
       store_c(out + bout + t * p.vos[0] + (int64_t)e * p.os, val, p.conj);
     }
   }
@@ -249,14 +253,15 @@ __device__ __forceinline__ void gb_pass_tile(const GbPass& p, const float2* in, 
     c.t = tid / p.tpt;
     c.u = tid - c.t * p.tpt;
   }
-  int64_t bin, bout, v0;
-  tile_origin(p, tile, &bin, &bout, &v0);
+  int64_t bin, bout, v0, vtw;
+  tile_origin(p, tile, &bin, &bout, &v0, &vtw);
   const int64_t left = p.vn[0] - v0;
   const int ntv = left < p.T ? (int)left : p.T;
   c.tvalid = c.t < ntv && c.u < p.tpt;
   c.bin = bin + c.t * p.vis[0];
   c.bout = bout + c.t * p.vos[0];
   c.v0 = v0 + c.t;
+  c.col = p.tw_dim ? vtw : c.v0;
   if (p.blue) {
     bluestein_tile(p, sm, c, bin, bout, ntv);
     return;
@@ -271,7 +276,7 @@ __device__ __forceinline__ void gb_pass_tile(const GbPass& p, const float2* in, 
     run_stage(p, s, sm, c, from_g, to_g);
   }
   if (p.store_mode == GB_MOVE_SMEM) {
-    tile_store(p, out, sm, bout, v0, ntv);
+    tile_store(p, out, sm, bout, v0, vtw, ntv);
     __syncthreads();
   }
 }

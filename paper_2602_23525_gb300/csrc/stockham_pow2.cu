@@ -49,12 +49,13 @@
 namespace {
 
 
-// Tensor map of a LOAD_ROWS input: dims (column, row, two vector loops),
-// the vector loops ordered by stride; swap = 1 when that order is (nb2, nb1).
+// Tensor map of a LOAD_ROWS input: dims (column, then the rows and the two
+// vector loops ordered by stride); pos = the map dims of the rows, nb1 and nb2
+// (packed as for map_coord).
 struct GbRowsMap {
   CUtensorMap map;
   int use;
-  int swap;
+  int pos;
 };
 
 // Thread -> (transform t, thread u within the transform):
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
           constexpr int BOXR = C::N < 256 ? C::N : 256;
 #pragma unroll
           for (int r0 = 0; r0 < C::N; r0 += BOXR)
-            tensor_copy_4d(smem_addr(dst + r0 * T), &rm.map, (int)c0, r0, rm.swap ? b2 : b1, rm.swap ? b1 : b2, bar);
+            tensor_copy_4d(smem_addr(dst + r0 * T), &rm.map, (int)c0, map_coord(rm.pos, 1, r0, b1, b2),
+                           map_coord(rm.pos, 2, r0, b1, b2), map_coord(rm.pos, 3, r0, b1, b2), bar);
         }
       } else {
         for (int e = lane; e < C::N; e += 32)
@@ -161,7 +163,11 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
     const bool valid = ts < cnt;
     float2* gout = k.out + ob + (int64_t)ts * k.vos0;
     const int64_t ostride = (STORE == GB_P2_STORE_COLS) ? k.os : 1;
-    const int64_t col = c0 + ts;  // post-twiddle column index (tile dimension)
+    int64_t col = c0 + ts;  // post-twiddle column index: the tile dimension's,
+    if (POSTTW && k.ptw_dim) {  // or that of a vector loop
+      const int64_t r = tile / cblocks;
+      col = k.ptw_dim == 1 ? r % k.nb1 : r / k.nb1;
+    }
     const float2* tile_buf = ibuf + b * TILE;
     if constexpr (LOAD == GB_P2_LOAD_ROWS)
       stage_in<LOGN, 0, true, T>(v, tile_buf + t0, k.twt, u0, k.conj);
@@ -189,10 +195,11 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
 
 
 // Tensor map for the LOAD_ROWS tiles of k: 8-byte elements, dims (V0 columns,
-// n rows, the two vector loops by increasing stride), box (T, min(n, 256), 1, 1).
-// Leaves rm->use = 0 (per-row bulk copies) when the layout has no such map:
-// an unaligned base, a stride that is not a multiple of 16 bytes or that
-// decreases along the dims, or an encoder error.
+// then the n rows and the two vector loops by increasing stride, extent-1
+// loops last), box T columns x min(n, 256) rows.  Leaves rm->use = 0 (per-row
+// bulk copies) when the layout has no such map: an unaligned base, a stride
+// that is not a multiple of 16 bytes or that decreases along the dims, or an
+// encoder error.
 void make_rows_map(const GbP2& k, int T, GbRowsMap* rm) {
   memset(rm, 0, sizeof(*rm));
   if (k.load != GB_P2_LOAD_ROWS || k.vis0 != 1) return;
@@ -201,31 +208,35 @@ void make_rows_map(const GbP2& k, int T, GbRowsMap* rm) {
   const int64_t n = int64_t(1) << k.logn;
   struct D {
     int64_t n, s;
-  } a{k.nb1, k.vis1 * 8}, b{k.nb2, k.vis2 * 8};
-  auto first = [](const D& x, const D& y) { return (x.n > 1) != (y.n > 1) ? x.n > 1 : x.s <= y.s; };
-  int swap = 0;
-  if (!first(a, b)) {
-    std::swap(a, b);
-    swap = 1;
-  }
-  if (k.is <= 0 || (a.n > 1 && a.s <= 0) || (b.n > 1 && b.s <= 0)) return;
-  cuuint64_t dim[4] = {(cuuint64_t)k.V0, (cuuint64_t)n, (cuuint64_t)a.n, (cuuint64_t)b.n};
-  cuuint64_t str[3] = {(cuuint64_t)(k.is * 8), (cuuint64_t)a.s, (cuuint64_t)b.s};
-  if (a.n == 1) str[1] = str[0] * n;  // extent-1 dims: any valid stride
-  if (b.n == 1) str[2] = str[1] * a.n;
+    int who;  // 0 rows, 1 nb1, 2 nb2
+  } d[3] = {{n, k.is * 8, 0}, {k.nb1, k.vis1 * 8, 1}, {k.nb2, k.vis2 * 8, 2}};
+  for (int i = 0; i < 3; ++i)
+    if (d[i].n > 1 && d[i].s <= 0) return;
+  auto before = [](const D& x, const D& y) { return (x.n > 1) != (y.n > 1) ? x.n > 1 : x.s < y.s; };
+  for (int i = 1; i < 3; ++i)  // stable insertion sort of three
+    for (int j = i; j > 0 && before(d[j], d[j - 1]); --j) std::swap(d[j], d[j - 1]);
+  cuuint64_t dim[4] = {(cuuint64_t)k.V0, (cuuint64_t)d[0].n, (cuuint64_t)d[1].n, (cuuint64_t)d[2].n};
+  cuuint64_t str[3] = {(cuuint64_t)d[0].s, (cuuint64_t)d[1].s, (cuuint64_t)d[2].s};
+  for (int i = 1; i < 3; ++i)
+    if (d[i].n == 1) str[i] = str[i - 1] * d[i - 1].n;  // extent-1 dims: any valid stride
   for (int i = 0; i < 3; ++i)
     if ((str[i] & 15) || str[i] >= (cuuint64_t(1) << 40)) return;
   if (str[0] < (cuuint64_t)(k.V0 * 8) || str[1] < str[0] || str[2] < str[1]) return;
   for (int i = 0; i < 4; ++i)
     if (dim[i] < 1 || dim[i] > (cuuint64_t(1) << 32)) return;
-  cuuint32_t box[4] = {(cuuint32_t)T, (cuuint32_t)(n < 256 ? n : 256), 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)T, 1, 1, 1};
+  int pos = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (d[i].who == 0) box[1 + i] = (cuuint32_t)(n < 256 ? n : 256);
+    pos |= (i + 1) << (2 * d[i].who);
+  }
   cuuint32_t es[4] = {1, 1, 1, 1};
   if (enc(&rm->map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<float2*>(k.in), dim, str, box, es,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return;
   rm->use = 1;
-  rm->swap = swap;
+  rm->pos = pos;
 }
 
 template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW>
@@ -427,11 +438,11 @@ void* gb_tensor_map_encoder() {
   return reinterpret_cast<void*>(fn);
 }
 
-int gb_p2_rows_map(const GbP2& k, int T, void* map, int* swap) {
+int gb_p2_rows_map(const GbP2& k, int T, void* map, int* pos) {
   GbRowsMap rm;
   make_rows_map(k, T, &rm);
   memcpy(map, &rm.map, sizeof(CUtensorMap));
-  *swap = rm.swap;
+  *pos = rm.pos;
   return rm.use;
 }
 

@@ -233,7 +233,7 @@ __device__ __forceinline__ void read_row(uint32_t tmem, int tid, float2* y) {
 
 template <int LOGN, int PREC, int LOAD, int STORE>
 __global__ void __launch_bounds__(256, 2) gb_tc_kernel(const __grid_constant__ GbP2 k,
-                                                       const __grid_constant__ CUtensorMap tm, int tmap, int swap) {
+                                                       const __grid_constant__ CUtensorMap tm, int tmap, int pos) {
   using C = TC<LOGN>;
   using P = Prec<PREC>;
   constexpr int T = (LOAD == GB_P2_LOAD_CONTIG && STORE == GB_P2_STORE_CONTIG) ? 4096 / C::N : 16;
@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(256, 2) gb_tc_kernel(const __grid_constant__ G
           constexpr int BOXR = C::N < 256 ? C::N : 256;
 #pragma unroll
           for (int r0 = 0; r0 < C::N; r0 += BOXR)
-            tensor_copy_4d(smem_addr(dst + r0 * T), &tm, (int)c0, r0, swap ? (int)b2 : (int)b1,
-                           swap ? (int)b1 : (int)b2, bar);
+            tensor_copy_4d(smem_addr(dst + r0 * T), &tm, (int)c0, map_coord(pos, 1, r0, (int)b1, (int)b2),
+                           map_coord(pos, 2, r0, (int)b1, (int)b2), map_coord(pos, 3, r0, (int)b1, (int)b2), bar);
         }
       } else {
         for (int e = lane; e < C::N; e += 32)
@@ -427,9 +427,9 @@ cudaError_t launch(const GbP2& k, cudaStream_t st) {
   if (grid < 1) return cudaSuccess;
   alignas(128) CUtensorMap tm;
   memset(&tm, 0, sizeof(tm));
-  int swap = 0, tmap = 0;
-  if (LOAD == GB_P2_LOAD_ROWS) tmap = gb_p2_rows_map(k, T, &tm, &swap);
-  fn<<<(unsigned)grid, 256, smem, st>>>(k, tm, tmap, swap);
+  int pos = 0, tmap = 0;
+  if (LOAD == GB_P2_LOAD_ROWS) tmap = gb_p2_rows_map(k, T, &tm, &pos);
+  fn<<<(unsigned)grid, 256, smem, st>>>(k, tm, tmap, pos);
   return cudaGetLastError();
 }
 

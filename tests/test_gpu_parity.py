@@ -155,6 +155,44 @@ def test_rank2_4096x4096():
     check([(n, n, n), (n, 1, 1)], [], -1, x, flags=EST, algo="ct")
 
 
+def _force(key, choice):
+    gbfft.fft_forget_wisdom()
+    gbfft.fft_import_wisdom(f"gbfft-wisdom 1\n{key}\t{choice}\n")
+
+
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fourstep_columns_innermost(sign):
+    """Four-step (eq. (2)) of transforms that run down columns: the scratch keeps
+    the unit-stride loop innermost, both passes tile along it and the pass-1
+    twiddle takes its column from a vector loop.  A rank-2 column dimension
+    (in place on the output), a rank-1 batch with two loops (out of place), and
+    the same with an input that is 8- but not 16-byte aligned (the generic pass
+    with the twiddle column from vector dim 1)."""
+    try:
+        x = u(4096 * 64, 91)
+        _force("r1 n=4096 is=64 os=64 v=[(64,1,1)] ip=1", "split:64")
+        err, info = check([(4096, 64, 64), (64, 1, 1)], [], sign, x, flags=EST, algo="ct")
+        assert "columns innermost" in info and "^(v1*k)" in info, info
+        x = u(4096 * 128 * 3 + 1, 92)
+        _force("r1 n=4096 is=128 os=128 v=[(3,524288,524288),(128,1,1)] ip=0", "split:64")
+        err, info = check([(4096, 128, 128)], [(128, 1, 1), (3, 524288, 524288)], sign, x, flags=EST, algo="ct")
+        assert "columns innermost" in info and "load=rows store=cols T=64" in info, info
+        err, info = check([(4096, 128, 128)], [(128, 1, 1), (3, 524288, 524288)], sign, x, flags=EST, algo="ct",
+                          in_offset=1)
+        assert "columns innermost" in info, info
+    finally:
+        gbfft.fft_forget_wisdom()
+
+
+def test_rank2_4096x4096_measured():
+    """The measuring planner over the rank-2 workload (its column dimension
+    chooses between one column-tile pass and a four-step)."""
+    n = 4096
+    x = u(n * n, fft_inputs.seed_for(1, 51))
+    err, info = check([(n, n, n), (n, 1, 1)], [], 1, x, flags=gbfft.FFT_MEASURE, algo="ct")
+    print(info)
+
+
 def test_rank3_256_cubed():
     n = 256
     x = u(n ** 3, fft_inputs.seed_for(3, 1))
@@ -255,8 +293,8 @@ def test_p2_strided_tile_shapes():
     x = u(1024 * 24, 60)
     err, info = check([(1024, 1, 24)], [(24, 1024, 1)], -1, x, flags=EST)
     assert "load=contig store=cols" in info
-    x = u(1024 * 20, 61)
-    err, info = check([(1024, 1, 20)], [(20, 1024, 1)], -1, x, flags=EST)
+    x = u(1024 * 18, 61)  # 18 columns: not a whole number of 4-column tiles
+    err, info = check([(1024, 1, 18)], [(18, 1024, 1)], -1, x, flags=EST)
     assert "p2-tma" not in info and "pass stockham" in info
 
 
