@@ -141,9 +141,14 @@ def test_plan_prime_is_bluestein():
 
 
 def test_plan_multidim_separable():
+    """Rank 2 is one rank-1 problem per dimension (sec. 4.2): the rows in one
+    pass, the 4096-long columns as a four-step whose scratch keeps the columns
+    innermost (both passes tile 64 adjacent columns)."""
     t = explain([(4096, 4096, 4096), (4096, 1, 1)])
     assert "separable rank-2" in t
-    assert t.count("pass stockham n=4096") == 2
+    assert t.count("pass stockham n=4096") == 1
+    assert "cooley-tukey n=4096 = 64 x 64" in t and "columns innermost" in t
+    assert t.count("load=rows store=cols T=64") == 2, t
 
 
 def test_size30_radix_decomposition():
