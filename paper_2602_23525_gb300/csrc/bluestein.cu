@@ -15,47 +15,84 @@
 
 namespace {
 
+// The standalone kernels walk transforms along blockIdx.y and the entries of
+// one transform along x, so that the offsets of a transform are computed once
+// per thread and the entry index needs no 64-bit division (the group
+// executor uses the per-element forms of gb_pointwise.cuh instead).
 __global__ void gb_blue_pre_kernel(const GbBlueIO b) {
-  const int64_t total = b.count * b.m;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
-    gb_blue_pre_elem(b, b.in, b.work, i, 0);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.y; v < b.count; v += gridDim.y) {
+    int64_t io, oo;
+    gb_pw_offsets(b, v, &io, &oo);
+    const float2* x = b.in + io;
+    float2* a = b.work + v * b.m;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < b.m; l += step) {
+      float2 val = make_float2(0.f, 0.f);
+      if (l < b.n) {
+        float2 xv = __ldg(x + l * b.is);
+        if (b.conj) xv.y = -xv.y;
+        val = gb_pw_cmul(xv, __ldg(b.w + l));
+      }
+      a[l] = val;
+    }
+  }
 }
 
 __global__ void gb_blue_mul_kernel(const GbBlueIO b, float2* data) {
-  const int64_t total = b.count * b.m;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
-    gb_blue_mul_elem(b, data, i);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.y; v < b.count; v += gridDim.y) {
+    float2* z = data + v * b.m;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < b.m; l += step) {
+      const float2 p = gb_pw_cmul(__ldcg(z + l), __ldg(b.B + l));
+      z[l] = make_float2(p.x, -p.y);
+    }
+  }
 }
 
 __global__ void gb_blue_post_kernel(const GbBlueIO b, const float2* data) {
-  const int64_t total = b.count * b.n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
-    gb_blue_post_elem(b, data, b.out, i);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.y; v < b.count; v += gridDim.y) {
+    int64_t io, oo;
+    gb_pw_offsets(b, v, &io, &oo);
+    const float2* d = data + v * b.m;
+    float2* y = b.out + oo;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b.n; k += step) {
+      float2 dv = __ldcg(d + k);
+      dv.y = -dv.y;
+      float2 r = gb_pw_cmul(dv, __ldg(b.w + k));
+      if (b.conj) r.y = -r.y;
+      y[k * b.os] = r;
+    }
+  }
 }
 
-unsigned grid_for(int64_t count) {
-  int64_t g = (count + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  if (g < 1) g = 1;
-  return (unsigned)g;
+// blocks along the transforms (y, one row each while they last) and along
+// the entries of a transform (x): about 32 x 152 blocks of 256 threads in
+// all, each thread taking several entries of one transform
+dim3 grid_for(int64_t count, int64_t len) {
+  const int64_t want = 152 * 32;
+  int64_t gy = count < 65535 ? count : 65535;
+  if (gy < 1) gy = 1;
+  int64_t gx = (want + gy - 1) / gy;
+  const int64_t most = (len + 255) / 256;
+  if (gx > most) gx = most;
+  if (gx < 1) gx = 1;
+  return dim3((unsigned)gx, (unsigned)gy);
 }
 
 }  // namespace
 
 cudaError_t gb_launch_blue_pre(const GbBlueIO& b, cudaStream_t st) {
-  gb_blue_pre_kernel<<<grid_for(b.count * b.m), 256, 0, st>>>(b);
+  gb_blue_pre_kernel<<<grid_for(b.count, b.m), 256, 0, st>>>(b);
   return cudaGetLastError();
 }
 
 cudaError_t gb_launch_blue_mul(const GbBlueIO& b, float2* data, cudaStream_t st) {
-  gb_blue_mul_kernel<<<grid_for(b.count * b.m), 256, 0, st>>>(b, data);
+  gb_blue_mul_kernel<<<grid_for(b.count, b.m), 256, 0, st>>>(b, data);
   return cudaGetLastError();
 }
 
 cudaError_t gb_launch_blue_post(const GbBlueIO& b, const float2* data, cudaStream_t st) {
-  gb_blue_post_kernel<<<grid_for(b.count * b.n), 256, 0, st>>>(b, data);
+  gb_blue_post_kernel<<<grid_for(b.count, b.n), 256, 0, st>>>(b, data);
   return cudaGetLastError();
 }

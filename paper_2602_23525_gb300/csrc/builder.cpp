@@ -240,8 +240,13 @@ struct Builder {
     line(depth, desc);
   }
 
+  static std::string epi_str(const GbP2Epi& e) {
+    static const char* what[] = {"", "Z = conj(y Bhat)", "y = w conj(D)", "y = conj(w conj(D))"};
+    return std::string(" epilogue ") + what[e.mode & 3] + " for k < " + std::to_string(e.K);
+  }
+
   bool make_single(const Dim& d, const std::vector<Dim>& Vin, int src, int dst, int conj, const PassCfg& cfg,
-                   const PostTw* tw, Step* out, std::string* desc) {
+                   const PostTw* tw, Step* out, std::string* desc, const GbP2Epi* epi = nullptr) {
     std::vector<Dim> V = Vin;
     if (V.empty()) V.push_back({1, 0, 0});
     if ((int)V.size() > GB_MAX_VDIMS || (int)cfg.radices.size() > GB_MAX_STAGES) {
@@ -285,6 +290,12 @@ struct Builder {
     p.ntiles = p.tiles0;
     for (int i = 1; i < p.nv; ++i) p.ntiles *= V[i].n;
     p.conj = conj;
+    if (epi) {
+      p.epi_tab = epi->tab;
+      p.epi_K = epi->K;
+      p.epi_kstride = epi->kstride;
+      p.epi_mode = epi->mode;
+    }
     if (tw) {
       p.post_tw = 1;
       p.tw_dim = tw->dim;
@@ -310,6 +321,7 @@ struct Builder {
       << " tpt=" << p.tpt << " threads=" << s.threads << " smem=" << s.smem << " tiles=" << p.ntiles
       << " vdims=" << dims_str(V);
     if (tw) o << " post-twiddle w_" << tw->N << "^(v" << tw->dim << "*k)";
+    if (epi) o << epi_str(*epi);
     if (conj) o << " conj";
     *out = s;
     *desc = o.str();
@@ -375,9 +387,10 @@ struct Builder {
   // ptw_dim: the post-twiddle column is the index along the tile dimension (0)
   // or along the pass's first / second other vector loop (1, 2; order_for_pass)
   void emit_p2(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t posttwN, int depth,
-               int ptw_dim = 0) {
+               int ptw_dim = 0, const GbP2Epi* epi = nullptr) {
     P2Choice c;
-    if (!p2_choose(d, V, posttwN > 0, &c, prec) || (ptw_dim && (c.prec || ptw_dim > (int)c.rest.size()))) {
+    if (!p2_choose(d, V, posttwN > 0, &c, prec) || (ptw_dim && (c.prec || ptw_dim > (int)c.rest.size())) ||
+        (epi && (c.prec || !gb_p2_epi_supported(c.logn, c.load, c.store, posttwN > 0 ? 1 : 0)))) {
       err = FFT_ERR_WISDOM;
       return;
     }
@@ -405,6 +418,7 @@ struct Builder {
     }
     k.conj = conj;
     k.ptw_dim = k.posttw ? ptw_dim : 0;
+    if (epi) k.epi = *epi;
     k.status = P->d_status;
     float2* tw = (float2*)dalloc(sizeof(float2) * (size_t)std::max(16, gb_p2_twiddle_elems(c.logn)));
     for (int st = 1; tw && !err; ++st) {
@@ -431,7 +445,7 @@ struct Builder {
     Step s;
     std::string desc;
     if (!make_single(d, VV, src, dst, conj, estimate_cfg(d, v0, !VV.empty(), default_radices(d.n)),
-                     k.posttw ? &tw2 : nullptr, &s, &desc))
+                     k.posttw ? &tw2 : nullptr, &s, &desc, epi))
       return;
     s.kind = STEP_POW2;
     s.p2 = k;
@@ -444,7 +458,7 @@ struct Builder {
       << " is=" << d.is << " os=" << d.os << " tile=" << dims_str({c.v0}) << " rest=" << dims_str(c.rest)
       << (k.posttw ? " post-twiddle w_" + std::to_string(posttwN) + "^(v" + std::to_string(ptw_dim) + "*k)"
                    : std::string())
-      << (conj ? " conj" : "")
+      << (epi ? epi_str(*epi) : std::string()) << (conj ? " conj" : "")
       << " (fallback: " << desc << ")";
     line(depth, o.str());
   }
@@ -807,6 +821,74 @@ struct Builder {
     solve_rank1({n2, 1, n1 * d.os}, V2, S, dst, conj, depth + 1);
   }
 
+  // Bluestein's convolution FFTs (m = n1 n2 a power of two, 2^14 .. 2^24) as
+  // two four-step passes each (eq. (2)) whose last pass applies the pointwise
+  // step as it stores: Z = conj(A Bhat) after the first FFT, y = w conj(D)
+  // straight into the output after the second (only k < n), so neither step
+  // makes a round trip through HBM of its own.  The work buffers hold the
+  // transforms contiguously, the caller's loops in order, the last fastest (as
+  // the pre step writes them); the output needs unit stride along k.
+  struct BlueFused {
+    int64_t n1, n2;
+    Dim d1, d2;
+    std::vector<Dim> V1, V2w, V2y;
+  };
+
+  bool blue_fused_plan(const Dim& d, const std::vector<Dim>& V, int64_t m, BlueFused* f) {
+    const int lg = log2_exact(m);
+    if (prec || lg < 14 || lg > 24 || d.os != 1 || V.size() > 2) return false;
+    f->n1 = (int64_t)1 << (lg / 2);
+    f->n2 = m / f->n1;
+    const int64_t n1 = f->n1, n2 = f->n2, count = prod_n(V);
+    f->d1 = {n1, n2, n2};  // [v][l1 n2 + l2] -> [v][k1 n2 + l2], twiddle w_m^{l2 k1}
+    f->V1 = {{n2, 1, 1}, {count, m, m}};
+    f->d2 = {n2, 1, n1};   // [v][k1 n2 + l2] -> Y[v][k1 + k2 n1]
+    f->V2w = {{n1, n2, 1}, {count, m, m}};
+    f->V2y = {{n1, n2, 1}};
+    int64_t st = m;
+    std::vector<Dim> Vy(V.size());
+    for (int i = (int)V.size() - 1; i >= 0; --i) {
+      Vy[i] = {V[i].n, st, V[i].os};
+      st *= V[i].n;
+    }
+    for (const Dim& v : Vy)
+      if (v.n > 1) f->V2y.push_back(v);
+    P2Choice c1, cw, cy;
+    if (!p2_choose(f->d1, f->V1, true, &c1) || !p2_choose(f->d2, f->V2w, false, &cw) ||
+        !p2_choose(f->d2, f->V2y, false, &cy))
+      return false;
+    if (!same_dim(c1.v0, f->V1[0]) || c1.load != GB_P2_LOAD_ROWS || c1.store != GB_P2_STORE_COLS) return false;
+    for (const P2Choice* c : {&cw, &cy})
+      if (!same_dim(c->v0, f->V2w[0]) || !gb_p2_epi_supported(c->logn, c->load, c->store, 0)) return false;
+    return true;
+  }
+
+  bool blue_fused_ok(const Dim& d, const std::vector<Dim>& V, int64_t m) {
+    BlueFused f;
+    return blue_fused_plan(d, V, m, &f);
+  }
+
+  void emit_blue_fused(const Dim& d, const std::vector<Dim>& V, int dst, int conj, int64_t m, const float2* w,
+                       const float2* B, int S0, int S1, int depth) {
+    BlueFused f;
+    if (!blue_fused_plan(d, V, m, &f)) {
+      err = FFT_ERR_UNSUPPORTED;
+      return;
+    }
+    std::ostringstream o;
+    o << "cooley-tukey m=" << m << " = " << f.n1 << " x " << f.n2 << " (eq. 2), the multiply fused into its store";
+    line(depth, o.str());
+    const GbP2Epi mul{B, m, f.n1, 1};
+    emit_p2(f.d1, f.V1, S0, S1, 0, m, depth + 1);
+    emit_p2(f.d2, f.V2w, S1, S0, 0, 0, depth + 1, 0, &mul);
+    std::ostringstream q;
+    q << "cooley-tukey m=" << m << " = " << f.n1 << " x " << f.n2 << " (eq. 2), y = w conj(D) fused into its store";
+    line(depth, q.str());
+    const GbP2Epi post{w, d.n, f.n1, conj ? 3 : 2};
+    emit_p2(f.d1, f.V1, S0, S1, 0, m, depth + 1);
+    emit_p2(f.d2, f.V2y, S1, dst, 0, 0, depth + 1, 0, &post);
+  }
+
   void emit_bluestein(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t m,
                       int depth) {
     const int64_t n = d.n;
@@ -887,6 +969,7 @@ struct Builder {
       return;
     }
     const int64_t count = prod_n(V);
+    const bool fuse = blue_fused_ok(d, V, m);
     const int S0 = new_scratch((size_t)count * m * sizeof(float2));
     const int S1 = new_scratch((size_t)count * m * sizeof(float2));
     GbBlueIO b;
@@ -912,6 +995,10 @@ struct Builder {
     pre.dst = S0;
     P->steps.push_back(pre);
     line(depth + 1, "pointwise a = pad(x w)");
+    if (fuse) {
+      emit_blue_fused(d, V, dst, conj, m, w, B, S0, S1, depth + 1);
+      return;
+    }
     solve_rank1({m, 1, 1}, {{count, m, m}}, S0, S1, 0, depth + 1);
     Step mul;
     mul.kind = STEP_BLUE_MUL;

@@ -18,6 +18,14 @@ int gb_pass_max_smem_optin(void);
 // vector loops (nb1, vis1, vos1), (nb2, vis2, vos2).
 enum { GB_P2_LOAD_CONTIG = 0, GB_P2_LOAD_ROWS = 1 };     // is == 1  |  vis0 == 1
 enum { GB_P2_STORE_CONTIG = 0, GB_P2_STORE_COLS = 1 };   // os == 1  |  vos0 == 1
+// Store epilogue of a last pass (Bluestein's pointwise steps, gb_epi_apply):
+// output k = col + (index along the transform) * kstride, col the tile
+// dimension's index; outputs with k >= K are not stored.  mode 0: none.
+struct GbP2Epi {
+  const float2* tab;
+  int64_t K, kstride;
+  int mode;
+};
 struct GbP2 {
   int logn, load, store, posttw;
   int prec;           // 0 FP32; tensor-core radix-16 stages: 1 FP16, 2 BF16, 3 FP16 split, 4 BF16 split
@@ -30,10 +38,12 @@ struct GbP2 {
   const float2* ptwA;  // post twiddle: A[c*L + j] = w_N^{c j}
   const float2* ptwB;  //               B[c] = (s, s^2, s^4, s^8), s = w_N^{c L}
   int ptw_dim;         // the column c: 0 the index along the tile dimension, 1 along nb1, 2 along nb2
+  GbP2Epi epi;         // store epilogue (LOAD_CONTIG / STORE_COLS without post twiddle only)
   int* status;
   int64_t grid;        // <= 0: persistent grid sized by occupancy
 };
 int gb_p2_supported(int logn, int load, int store, int posttw);
+int gb_p2_epi_supported(int logn, int load, int store, int posttw);  // a store epilogue is built
 // tensor map (128 bytes at map, 64-byte aligned) of the LOAD_ROWS tiles of k
 // with T columns: dims (V0, then the rows and the two vector loops ordered by
 // stride), box T x min(n, 256) rows; returns 0 when the layout has none;

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "codelets.cuh"
+#include "gb_pointwise.cuh"
 
 namespace {
 
@@ -114,10 +115,26 @@ __device__ __forceinline__ void stage_out_x(const float2* v, float2* dst, int u)
 // Last stage writes global memory: output k = j + q*L of the transform goes
 // to dst[k * ostride].  POSTTW multiplies output k of column l2 by
 // w_N^{l2 k} = A[l2 L + j] * s^q with s = w_N^{l2 L} from B[l2] = (s, s^2, s^4, s^8).
-template <int LOGN, bool POSTTW>
+// PW applies the store epilogue e (outputs col + k * e->kstride >= e->K skipped).
+// The table entries of the epilogue, for the last stage's outputs of thread u
+// (loaded at the start of a tile, so that their latency hides behind the stages).
+template <int LOGN>
+__device__ __forceinline__ void epi_prefetch(float2* t, const GbP2Epi* e, int u, int64_t col) {
+  using C = P2<LOGN>;
+  constexpr int S = C::NST - 1;
+  constexpr int R = C::radix(S), L = C::L(S);
+  static_assert(R == 16, "the epilogue needs a radix-16 last stage");
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int64_t kk = col + (int64_t)(u + q * L) * e->kstride;
+    t[q] = kk < e->K ? __ldg(e->tab + kk) : make_float2(0.f, 0.f);
+  }
+}
+
+template <int LOGN, bool POSTTW, bool PW = false>
 __device__ __forceinline__ void stage_out_g(const float2* v, float2* dst, int64_t ostride, int u, int conj,
                                             const float2* __restrict__ A, const float2* __restrict__ Bt,
-                                            int64_t col) {
+                                            int64_t col, const GbP2Epi* e = nullptr, const float2* t = nullptr) {
   using C = P2<LOGN>;
   constexpr int S = C::NST - 1;
   constexpr int R = C::radix(S), B = 16 / R, L = C::L(S);
@@ -131,32 +148,39 @@ __device__ __forceinline__ void stage_out_g(const float2* v, float2* dst, int64_
       powers16(p, reinterpret_cast<const float4*>(Bt + col * 4));
       a = __ldg(A + col * L + j);
     }
+    if constexpr (PW) static_assert(B == 1, "the epilogue needs a radix-16 last stage");
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       float2 x = v[b * R + q];
       if constexpr (POSTTW) x = cmul(x, q == 0 ? a : cmul(a, p[q]));
+      if constexpr (PW) {
+        if (col + (int64_t)(j + q * L) * e->kstride >= e->K) continue;
+        x = gb_epi_apply(e->mode, x, t[q]);  // t: epi_prefetch
+      }
       if (conj) x.y = -x.y;
       dst[(int64_t)(j + q * L) * ostride] = x;
     }
   }
 }
 
-template <int LOGN, int S, bool POSTTW>
+template <int LOGN, int S, bool POSTTW, bool PW = false>
 __device__ __forceinline__ void later_stages(float2* v, float2* xrow_j, float2* xrow_s, float2* gout,
                                              int64_t ostride, const float2* __restrict__ twt, int uj, int us,
-                                             int conj, bool valid, const float2* A, const float2* Bt, int64_t col) {
+                                             int conj, bool valid, const float2* A, const float2* Bt, int64_t col,
+                                             const GbP2Epi* e = nullptr, const float2* t = nullptr) {
   using C = P2<LOGN>;
   if constexpr (S < C::NST) {
     if constexpr (S == C::NST - 1) {
       // the last stage runs in the store mapping
       stage_in<LOGN, S, false, 1>(v, xrow_s, twt, us, conj);
-      if (valid) stage_out_g<LOGN, POSTTW>(v, gout, ostride, us, conj, A, Bt, col);
+      if (valid) stage_out_g<LOGN, POSTTW, PW>(v, gout, ostride, us, conj, A, Bt, col, e, t);
     } else {
       stage_in<LOGN, S, false, 1>(v, xrow_j, twt, uj, conj);
       __syncthreads();
       stage_out_x<LOGN, S>(v, xrow_j, uj);
       __syncthreads();
-      later_stages<LOGN, S + 1, POSTTW>(v, xrow_j, xrow_s, gout, ostride, twt, uj, us, conj, valid, A, Bt, col);
+      later_stages<LOGN, S + 1, POSTTW, PW>(v, xrow_j, xrow_s, gout, ostride, twt, uj, us, conj, valid, A, Bt, col,
+                                            e, t);
     }
   }
 }

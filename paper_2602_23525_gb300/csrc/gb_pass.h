@@ -65,6 +65,11 @@ struct GbPass {
   int64_t twS;          // w_N^m = hi[m / S] * lo[m % S]
   const float2* tw_lo;  // lo[i] = w_N^i,      i < S
   const float2* tw_hi;  // hi[i] = w_N^{i S},  i <= N / S
+  // ---- store epilogue (Bluestein's pointwise steps, gb_epi_apply) --------------
+  const float2* epi_tab;  // table by output k = v0 + (index along the transform) * epi_kstride
+  int64_t epi_K;          // outputs with k >= epi_K are not stored
+  int64_t epi_kstride;
+  int epi_mode;           // 0: none
   // ---- fused Bluestein (n = m, the convolution length) ------------------------
   int blue;             // 1: Y[k] = w_k * IDFT_m( DFT_m(x w) * Bhat )[k], k < bn
   int bn;               // true transform length (prime)

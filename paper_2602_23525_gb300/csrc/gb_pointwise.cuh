@@ -13,6 +13,20 @@ __device__ __forceinline__ float2 gb_pw_cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Bluestein's pointwise steps applied to an FFT output y as it is stored
+// (the store epilogue of the last pass, table entry t = tab[k]):
+//   mode 1 (mul):  conj(y t)          with t = Bhat[k]
+//   mode 2 (post): t conj(y)          with t = w_k (forward)
+//   mode 3 (post): conj(t conj(y))    (backward: the output conjugated)
+__device__ __forceinline__ float2 gb_epi_apply(int mode, float2 y, float2 t) {
+  if (mode == 1) {
+    const float2 z = gb_pw_cmul(y, t);
+    return make_float2(z.x, -z.y);
+  }
+  const float2 z = gb_pw_cmul(t, make_float2(y.x, -y.y));
+  return mode == 3 ? make_float2(z.x, -z.y) : z;
+}
+
 __device__ __forceinline__ void gb_pw_offsets(const GbBlueIO& b, int64_t v, int64_t* io, int64_t* oo) {
   int64_t a = 0, c = 0;
   for (int d = b.nv - 1; d >= 0; --d) {

@@ -114,6 +114,11 @@ __device__ __forceinline__ void stage(const GbPass& p, int s, float2* sm, const 
           const int idx = base + q * L;
           float2 val = v[b][q];
           if (p.post_tw) val = cmul(val, split_twiddle(p, c.col * (int64_t)idx));
+          if (p.epi_mode) {
+            const int64_t kk = c.v0 + (int64_t)idx * p.epi_kstride;
+            if (kk >= p.epi_K) continue;
+            val = gb_epi_apply(p.epi_mode, val, __ldg(p.epi_tab + kk));
+          }
           store_c(dst + (int64_t)idx * p.os, val, p.conj);
         }
       } else {
@@ -194,6 +199,11 @@ __device__ void tile_store(const GbPass& p, float2* out, const float2* sm, int64
     if (t < ntv) {
       float2 val = sm[t * p.pitch + phys(e)];
       if (p.post_tw) val = cmul(val, split_twiddle(p, (p.tw_dim ? vtw : v0 + t) * (int64_t)e));
+      if (p.epi_mode) {
+        const int64_t kk = v0 + t + (int64_t)e * p.epi_kstride;
+        if (kk >= p.epi_K) continue;
+        val = gb_epi_apply(p.epi_mode, val, __ldg(p.epi_tab + kk));
+      }
       store_c(out + bout + t * p.vos[0] + (int64_t)e * p.os, val, p.conj);
     }
   }

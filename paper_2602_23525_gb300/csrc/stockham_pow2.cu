@@ -63,7 +63,7 @@ struct GbRowsMap {
 //   "t-fast": t = tid % T,   u = tid / T   (lanes across the T transforms)
 // Stage 0 uses the mapping that reads the landed tile without bank conflicts,
 // the last stage the one that makes the global stores coalesce.
-template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW>
+template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW, bool PW>
 __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
     gb_p2_kernel(const __grid_constant__ GbP2 k, const __grid_constant__ GbRowsMap rm) {
   using C = P2<LOGN>;
@@ -169,6 +169,8 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
       col = k.ptw_dim == 1 ? r % k.nb1 : r / k.nb1;
     }
     const float2* tile_buf = ibuf + b * TILE;
+    float2 et[PW ? 16 : 1];
+    if constexpr (PW) epi_prefetch<LOGN>(et, &k.epi, us, col);
     if constexpr (LOAD == GB_P2_LOAD_ROWS)
       stage_in<LOGN, 0, true, T>(v, tile_buf + t0, k.twt, u0, k.conj);
     else
@@ -183,12 +185,12 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
     }
     if constexpr (C::NST == 1) {
       // one stage: the host only builds this when both mappings agree
-      if (valid) stage_out_g<LOGN, POSTTW>(v, gout, ostride, u0, k.conj, k.ptwA, k.ptwB, col);
+      if (valid) stage_out_g<LOGN, POSTTW, PW>(v, gout, ostride, u0, k.conj, k.ptwA, k.ptwB, col, &k.epi, et);
     } else {
       stage_out_x<LOGN, 0>(v, xbuf + t0 * C::PITCH, u0);
       __syncthreads();
-      later_stages<LOGN, 1, POSTTW>(v, xbuf + tj * C::PITCH, xbuf + ts * C::PITCH, gout, ostride, k.twt, uj, us,
-                                    k.conj, valid, k.ptwA, k.ptwB, col);
+      later_stages<LOGN, 1, POSTTW, PW>(v, xbuf + tj * C::PITCH, xbuf + ts * C::PITCH, gout, ostride, k.twt, uj, us,
+                                    k.conj, valid, k.ptwA, k.ptwB, col, &k.epi, et);
     }
   }
 }
@@ -239,12 +241,12 @@ void make_rows_map(const GbP2& k, int T, GbRowsMap* rm) {
   rm->pos = pos;
 }
 
-template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW>
+template <int LOGN, int T, int NBUF, int MINB, int LOAD, int STORE, bool POSTTW, bool PW>
 cudaError_t launch(const GbP2& k, cudaStream_t st) {
   using C = P2<LOGN>;
   static_assert(LOAD != GB_P2_LOAD_ROWS || (T % 2 == 0), "tensor-map boxes need 16-byte rows");
   const size_t smem = 128 + sizeof(float2) * ((size_t)NBUF * T * C::N + (C::NST > 1 ? (size_t)T * C::PITCH : 0));
-  auto fn = gb_p2_kernel<LOGN, T, NBUF, MINB, LOAD, STORE, POSTTW>;
+  auto fn = gb_p2_kernel<LOGN, T, NBUF, MINB, LOAD, STORE, POSTTW, PW>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -391,9 +393,25 @@ constexpr int min_blocks(int logn, int load, int store) {
   return (load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG) ? (logn <= 12 ? 2 : 1) : (logn <= 8 ? 2 : 1);
 }
 
-template <int LOGN, int LOAD, int STORE, bool POSTTW>
+template <int LOGN, int LOAD, int STORE, bool POSTTW, bool PW = false>
 cudaError_t launch_n(const GbP2& k, cudaStream_t st) {
-  return launch<LOGN, tile_T(LOGN, LOAD, STORE), 2, min_blocks(LOGN, LOAD, STORE), LOAD, STORE, POSTTW>(k, st);
+  return launch<LOGN, tile_T(LOGN, LOAD, STORE), 2, min_blocks(LOGN, LOAD, STORE), LOAD, STORE, POSTTW, PW>(k, st);
+}
+
+// the store epilogue: contiguous transforms in, column tiles out (the last
+// pass of a four-step), n = 2^6 .. 2^12
+cudaError_t dispatch_epi(const GbP2& k, cudaStream_t st) {
+  constexpr int LD = GB_P2_LOAD_CONTIG, SC = GB_P2_STORE_COLS;
+  switch (k.logn) {
+    case 6: return launch_n<6, LD, SC, false, true>(k, st);
+    case 7: return launch_n<7, LD, SC, false, true>(k, st);
+    case 8: return launch_n<8, LD, SC, false, true>(k, st);
+    case 9: return launch_n<9, LD, SC, false, true>(k, st);
+    case 10: return launch_n<10, LD, SC, false, true>(k, st);
+    case 11: return launch_n<11, LD, SC, false, true>(k, st);
+    case 12: return launch_n<12, LD, SC, false, true>(k, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int LOAD, int STORE, bool POSTTW>
@@ -446,6 +464,10 @@ int gb_p2_rows_map(const GbP2& k, int T, void* map, int* pos) {
   return rm.use;
 }
 
+int gb_p2_epi_supported(int logn, int load, int store, int posttw) {
+  return load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_COLS && !posttw && logn >= 6 && logn <= 12;
+}
+
 int gb_p2_supported(int logn, int load, int store, int posttw) {
   const bool cc = load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG;
   if (cc) return !posttw && logn >= 4 && logn <= 13;
@@ -486,6 +508,8 @@ int gb_p2_last_L(int logn) {
 }
 
 cudaError_t gb_launch_p2(const GbP2& k, cudaStream_t st) {
+  if (k.epi.mode)
+    return gb_p2_epi_supported(k.logn, k.load, k.store, k.posttw) ? dispatch_epi(k, st) : cudaErrorInvalidValue;
   if (k.load == GB_P2_LOAD_CONTIG && k.store == GB_P2_STORE_CONTIG)
     return dispatch<GB_P2_LOAD_CONTIG, GB_P2_STORE_CONTIG, false>(k, st);
   if (k.load == GB_P2_LOAD_CONTIG && k.store == GB_P2_STORE_COLS)

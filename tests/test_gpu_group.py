@@ -60,6 +60,27 @@ def run_group(probs, sign, stream, flags=0, repeat=1):
 MODES = [gbfft.FFT_GROUP_PERSISTENT, gbfft.FFT_GROUP_GRAPH, 0]
 
 
+@pytest.mark.parametrize("flags", MODES)
+def test_group_with_fused_bluestein(flags):
+    """A plan whose Bluestein steps ride on the FFT stores (store epilogues)
+    in a group: the persistent queue runs their generic passes with the same
+    epilogue."""
+    gbfft.fft_forget_wisdom()
+    gbfft.fft_import_wisdom("gbfft-wisdom 1\nr1 n=10007 is=1 os=1 v=[(4,10007,10007)] ip=0\tblue:32768\n")
+    try:
+        probs = [(10007, [(10007, 1, 1)], [(4, 10007, 10007)], fft_inputs.gaussian_c64(10007 * 4, 95)),
+                 (1000, [(1000, 1, 1)], [(4, 1000, 1000)], fft_inputs.gaussian_c64(4000, 96))]
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            outs, alone, status = run_group(probs, 1, s.cuda_stream, flags=flags)
+        assert status == gbfft.FFT_OK
+        for (n, dims, how, x), y, a in zip(probs, outs, alone):
+            ref = reference(dims, how, 1, x, algo="ct" if n > 4096 else "auto")
+            assert per_transform_error(y, ref, dims, how).max() <= TOL, n
+    finally:
+        gbfft.fft_forget_wisdom()
+
+
 @pytest.mark.parametrize("sign", [-1, 1])
 @pytest.mark.parametrize("flags", MODES)
 def test_uneven_group_matches_oracle_and_alone(sign, flags):

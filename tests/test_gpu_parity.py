@@ -184,6 +184,29 @@ def test_fourstep_columns_innermost(sign):
         gbfft.fft_forget_wisdom()
 
 
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_bluestein_fused_fourstep(sign):
+    """Bluestein (sec. 4.2, prime sizes) with m a power of two beyond one CTA:
+    the multiply and the output step ride on the stores of the last passes of
+    the two convolution FFTs.  n = 10007 (m = 2^15, contiguous), and n = 8193
+    (m = 2^16) with two padded vector loops, out of place with an output
+    offset (8-byte aligned stores) and an input offset."""
+    try:
+        b = 8
+        x = u(10007 * b, 93)
+        _force(f"r1 n=10007 is=1 os=1 v=[({b},10007,10007)] ip=0", "blue:32768")
+        err, info = check([(10007, 1, 1)], [(b, 10007, 10007)], sign, x, flags=EST, algo="ct")
+        assert "multiply fused" in info and "epilogue" in info and "pointwise Z" not in info, info
+        how = [(3, 8193, 8193), (2, 3 * 8193 + 5, 2 * 3 * 8193 + 7)]
+        x = u(2 * (3 * 8193 + 5) + 8, 94)
+        _force("r1 n=8193 is=1 os=1 v=[(2,24584,49165),(3,8193,8193)] ip=0", "blue:65536")
+        err, info = check([(8193, 1, 1)], how, sign, x, flags=EST, algo="ct", out_offset=1)
+        assert "y = " in info and "epilogue" in info, info
+        err, info = check([(8193, 1, 1)], how, sign, x, flags=EST, algo="ct", in_offset=3)
+    finally:
+        gbfft.fft_forget_wisdom()
+
+
 def test_rank2_4096x4096_measured():
     """The measuring planner over the rank-2 workload (its column dimension
     chooses between one column-tile pass and a four-step)."""
