@@ -1,4 +1,4 @@
-"""Run and time one DFT problem from the command line.
+r"""Run and time one DFT problem from the command line.
 
     python -m paper_2602_23525_gb300.cli --dims 4096,1,1 --howmany 8192,4096,4096 \
         --sign -1 --reps 5 [--estimate]
@@ -6,6 +6,9 @@
 Dimensions are "n,is,os" triples (strides in complex elements), as in
 dft(N, V, I, O).  Prints the plan tree and the median device time per
 execution with its GFLOP/s (5 N log2 N) and algorithmic GB/s (16 B/point).
+--wisdom takes wisdom entries ("key\tchoice" lines, with \t and \n written
+as escapes) to import before planning, e.g. to replay one plan choice:
+    --wisdom 'r1 n=10007 is=1 os=1 v=[(512,10007,10007)] ip=0\tblue:32768'
 """
 import argparse
 import math
@@ -30,10 +33,14 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--estimate", action="store_true")
     ap.add_argument("--inplace", action="store_true")
+    ap.add_argument("--wisdom", default="")
     a = ap.parse_args(argv)
     import torch
 
     from . import gbfft
+    if a.wisdom:
+        body = a.wisdom.replace("\\t", "\t").replace("\\n", "\n")
+        gbfft.fft_import_wisdom("gbfft-wisdom 1\n" + body.rstrip("\n") + "\n")
     dims, how = parse_dims(a.dims), parse_dims(a.howmany)
     flags = (gbfft.FFT_ESTIMATE if a.estimate else 0) | (gbfft.FFT_INPLACE if a.inplace else 0)
 
