@@ -33,8 +33,8 @@ def uneven_problems(batch):
     return probs
 
 
-def run_group(probs, sign, stream, flags=0, repeat=1):
-    plans = [gbfft.Plan(d, h, sign, EST) for _, d, h, _ in probs]
+def run_group(probs, sign, stream, flags=0, repeat=1, plan_flags=EST):
+    plans = [gbfft.Plan(d, h, sign, plan_flags) for _, d, h, _ in probs]
     ins = [torch.from_numpy(x).cuda() for *_, x in probs]
     outs = [torch.zeros_like(t) for t in ins]
     g = gbfft.fft_group_create([p.handle for p in plans], flags)
@@ -148,14 +148,17 @@ def test_group_wait_timeout_is_reported_and_context_survives():
     p.destroy()
 
 
-def test_uneven_full_size_sampled():
-    """The full uneven workload (6 sizes x 512, mixed layouts) in one launch;
-    sampled transforms (first, middle, last of each size) against the oracle."""
+@pytest.mark.parametrize("plan_flags", [EST, gbfft.FFT_MEASURE])
+def test_uneven_full_size_sampled(plan_flags):
+    """The full uneven workload (6 sizes x 512, mixed layouts) in one group
+    execution, with estimated plans and with the measured plans the benchmark
+    runs; sampled transforms (first, middle, last of each size) against the
+    oracle."""
     batch = fft_inputs.UNEVEN_BATCH
     probs = uneven_problems(batch)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        outs, alone, status = run_group(probs, -1, s.cuda_stream)
+        outs, alone, status = run_group(probs, -1, s.cuda_stream, plan_flags=plan_flags)
     assert status == gbfft.FFT_OK
     for (n, dims, how, x), y in zip(probs, outs):
         for v in (0, batch // 2, batch - 1):

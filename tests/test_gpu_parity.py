@@ -71,6 +71,36 @@ def test_large_multipass(n):
     check([(n, 1, 1)], [], -1, x, flags=EST, algo="ct")
 
 
+@pytest.mark.parametrize("exps", [range(4, 10), range(10, 15), range(15, 19), range(19, 22), range(22, 25)])
+def test_sweep_full_size_measured_sampled(exps):
+    """The benchmark step's transforms at their full sizes (2^26 points: n = 2^e,
+    batch 2^26 / n) with the plans the measuring planner picks, as the bench
+    runs them; sampled transforms (first, middle, last) against the oracle."""
+    total = 2 ** 26
+    x = torch.from_numpy(u(total, fft_inputs.seed_for(1, 98))).cuda()
+    y = torch.empty_like(x)
+    for e in exps:
+        n, sign = 2 ** e, (-1 if e % 2 == 0 else 1)
+        b = total // n
+        p = gbfft.Plan([(n, 1, 1)], [(b, n, n)], sign, gbfft.FFT_MEASURE)
+        p.execute(x, y)
+        torch.cuda.synchronize()
+        for v in sorted({0, b // 2, b - 1}):
+            xi = x[v * n:(v + 1) * n].cpu().numpy()
+            yi = y[v * n:(v + 1) * n].cpu().numpy()
+            ref = reference([(n, 1, 1)], [], sign, xi, algo="ct" if n > 4096 else "auto")
+            err = np.linalg.norm(yi.astype(np.complex128) - ref) / np.linalg.norm(ref)
+            assert err <= TOL, (n, v, err, p.info)
+        p.destroy()
+
+
+def test_single_2_24_measured():
+    """The single 2^24-point transform with the measured plan (as the bench)."""
+    n = 2 ** 24
+    x = u(n, fft_inputs.seed_for(1, 97))
+    check([(n, 1, 1)], [], 1, x, flags=gbfft.FFT_MEASURE, algo="ct")
+
+
 def test_single_2_24():
     n = 2 ** 24
     x = u(n, fft_inputs.seed_for(1, 99))
