@@ -472,7 +472,7 @@ int gb_p2_supported(int logn, int load, int store, int posttw) {
   const bool cc = load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG;
   if (cc) return !posttw && logn >= 4 && logn <= 13;
   if (logn < 6 || logn > 12) return 0;
-  if (posttw && !(load == GB_P2_LOAD_ROWS && store == GB_P2_STORE_COLS)) return 0;
+  if (posttw && load != GB_P2_LOAD_ROWS) return 0;
   if (posttw && logn % 4 != 0 && logn / 4 + 1 < 2) return 0;
   return 1;
 }
@@ -515,7 +515,8 @@ cudaError_t gb_launch_p2(const GbP2& k, cudaStream_t st) {
   if (k.load == GB_P2_LOAD_CONTIG && k.store == GB_P2_STORE_COLS)
     return dispatch<GB_P2_LOAD_CONTIG, GB_P2_STORE_COLS, false>(k, st);
   if (k.load == GB_P2_LOAD_ROWS && k.store == GB_P2_STORE_CONTIG)
-    return dispatch<GB_P2_LOAD_ROWS, GB_P2_STORE_CONTIG, false>(k, st);
+    return k.posttw ? dispatch<GB_P2_LOAD_ROWS, GB_P2_STORE_CONTIG, true>(k, st)
+                    : dispatch<GB_P2_LOAD_ROWS, GB_P2_STORE_CONTIG, false>(k, st);
   if (k.load == GB_P2_LOAD_ROWS && k.store == GB_P2_STORE_COLS)
     return k.posttw ? dispatch<GB_P2_LOAD_ROWS, GB_P2_STORE_COLS, true>(k, st)
                     : dispatch<GB_P2_LOAD_ROWS, GB_P2_STORE_COLS, false>(k, st);

@@ -237,6 +237,30 @@ def test_bluestein_fused_fourstep(sign):
         gbfft.fft_forget_wisdom()
 
 
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fourstep_batch_fastest_input(sign):
+    """Four-step (eq. (2)) of a batch-fastest input with transform-contiguous
+    output: the scratch [l2][b][k1]; pass 1 loads rows of adjacent transforms
+    and stores whole transforms with the twiddle column taken from a vector
+    loop, pass 2 loads rows of adjacent k1.  One loop and two loops (padded
+    strides), and an input that is 8- but not 16-byte aligned (the generic
+    passes)."""
+    try:
+        x = u(4096 * 64, 101)
+        _force("r1 n=4096 is=64 os=1 v=[(64,1,4096)] ip=0", "split:64")
+        err, info = check([(4096, 64, 1)], [(64, 1, 4096)], sign, x, flags=EST, algo="ct")
+        assert "scratch [l2][b][k1]" in info and "load=rows store=contig" in info, info
+        how = [(64, 1, 4096), (3, 4096 * 64 + 8, 4096 * 64 + 16)]
+        x = u(3 * (4096 * 64 + 8) + 4, 102)
+        _force("r1 n=4096 is=64 os=1 v=[(3,262152,262160),(64,1,4096)] ip=0", "split:64")
+        err, info = check([(4096, 64, 1)], how, sign, x, flags=EST, algo="ct")
+        assert "scratch [l2][b][k1]" in info and "^(v2*k)" in info, info
+        err, info = check([(4096, 64, 1)], how, sign, x, flags=EST, algo="ct", in_offset=1)
+        assert "scratch [l2][b][k1]" in info, info
+    finally:
+        gbfft.fft_forget_wisdom()
+
+
 def test_rank2_4096x4096_measured():
     """The measuring planner over the rank-2 workload (its column dimension
     chooses between one column-tile pass and a four-step)."""
