@@ -209,3 +209,42 @@ def test_cluster_plans_and_wisdom():
             gbfft.fft_import_wisdom(f"gbfft-wisdom 1\n{key}\t{bad}\n")
         assert ei.value.code == gbfft.FFT_ERR_WISDOM
     gbfft.fft_forget_wisdom()
+
+
+def test_plan_layout_specific_four_steps():
+    """The four-step (eq. (2)) picks its scratch layout from the problem's
+    strides: columns innermost for transforms down the columns of a row-major
+    array, [l2][b][k1] for a batch-fastest input into transform-contiguous
+    output (from 2^14 on in estimate mode; shorter ones transpose first), and
+    the plain [vector][k1][l2] for contiguous batches."""
+    t = explain([(65536, 512, 1)], [(512, 1, 65536)])
+    assert "batch-fastest input, scratch [l2][b][k1]" in t and "transpose first" not in t, t
+    assert t.count("pass p2-tma") == 2 and "load=rows store=contig" in t and "^(v1*k)" in t, t
+    t = explain([(4096, 512, 1)], [(512, 1, 4096)])
+    assert "transpose first" in t, t
+    t = explain([(8192, 64, 64), (64, 1, 1)])
+    assert "columns innermost" in t and t.count("load=rows store=cols T=64") == 1, t
+    t = explain([(65536, 1, 1)], [(8, 65536, 65536)])
+    assert "cooley-tukey n=65536" in t and "columns innermost" not in t and "[l2][b][k1]" not in t, t
+    # a column count that no 64-column tile divides keeps the column-tile pass
+    t = explain([(4096, 40, 40), (40, 1, 1)])
+    assert "columns innermost" not in t, t
+
+
+def test_plan_bluestein_store_epilogues():
+    """Bluestein with a power-of-two convolution length (sec. 4.2.5 prime sizes):
+    the multiply and the output step ride on the stores of the FFT passes;
+    a smooth non-power-of-two length keeps the separate pointwise steps."""
+    gbfft.fft_forget_wisdom()
+    try:
+        gbfft.fft_import_wisdom("gbfft-wisdom 1\nr1 n=10007 is=1 os=1 v=[(8,10007,10007)] ip=0\tblue:32768\n")
+        t = explain([(10007, 1, 1)], [(8, 10007, 10007)])
+        assert "multiply fused" in t and "epilogue Z = conj(y Bhat) for k < 32768" in t, t
+        assert "epilogue y = w conj(D) for k < 10007" in t and "pointwise Z" not in t, t
+        t = explain([(10007, 1, 1)], [(8, 10007, 10007)], sign=1)
+        assert "epilogue y = conj(w conj(D))" in t, t
+        gbfft.fft_forget_wisdom()
+        t = explain([(10007, 1, 1)], [(8, 10007, 10007)])
+        assert "bluestein n=10007 m=20160" in t and "pointwise Z = conj(A Bhat)" in t, t
+    finally:
+        gbfft.fft_forget_wisdom()
