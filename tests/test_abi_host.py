@@ -244,7 +244,14 @@ def test_plan_bluestein_store_epilogues():
         t = explain([(10007, 1, 1)], [(8, 10007, 10007)], sign=1)
         assert "epilogue y = conj(w conj(D))" in t, t
         gbfft.fft_forget_wisdom()
+        # estimate mode: the fused power of two where the smooth length would
+        # need several passes; the smooth length where it fits one CTA or where
+        # the output layout rules out the fused stores (stride 2 along k)
         t = explain([(10007, 1, 1)], [(8, 10007, 10007)])
+        assert "bluestein n=10007 m=32768" in t and "multiply fused" in t, t
+        t = explain([(4099, 1, 1)], [(8, 4099, 4099)])
+        assert "bluestein n=4099 m=8232" in t and "bluestein-fused" in t, t
+        t = explain([(10007, 1, 2)], [(8, 10007, 20014)])
         assert "bluestein n=10007 m=20160" in t and "pointwise Z = conj(A Bhat)" in t, t
     finally:
         gbfft.fft_forget_wisdom()
