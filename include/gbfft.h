@@ -235,9 +235,13 @@ void fft_group_destroy(fft_group g);
  * output buffers (pinned memory gives asynchronous copies).  A worker thread
  * admits waiting requests in arrival order whenever their device work buffers
  * (input, output and plan scratch, carved from one pool of `budget_bytes`) fit
- * in the unused budget and one of `nstreams` streams has a free slot; waiting
- * requests with the same shape and sign are merged into one launch.  Copies and
- * transforms of different launches overlap on the device.  Plans stay cached.
+ * in the unused budget and one of `nstreams` compute streams has a free slot;
+ * waiting requests with the same shape and sign are merged into one launch.
+ * Each launch is a pipeline over streams joined by events: its host->device
+ * copies on one copy-in stream (admission order), the transform on a compute
+ * stream, its device->host copies on one copy-out stream, so both directions
+ * of the host link and the transforms of different launches overlap.  Plans
+ * stay cached; making one does not synchronise the device.
  *   fft_server_create : budget_bytes >= 4096, nstreams in [1, 64], flags 0;
  *                       allocates the pool on the current device.
  *   fft_server_submit : enqueues; `arrival` is the request's arrival time in
@@ -250,7 +254,9 @@ void fft_group_destroy(fft_group g);
  *   fft_server_drain  : waits until nothing is queued or running (1 on timeout).
  *   fft_server_stats  : JSON text (completed, launches, merged requests, p50 /
  *                       p99 latency from arrival to completion, throughput,
- *                       budget high-water mark); length as fft_plan_info.
+ *                       budget high-water mark, cached plans, and the seconds
+ *                       the queue head waited for a stream slot or for
+ *                       memory); length as fft_plan_info.
  *   fft_server_destroy: finishes queued work, then frees everything.
  */
 typedef struct fft_server_s *fft_server;
