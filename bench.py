@@ -259,12 +259,13 @@ def run_gpu(args, rank, world):
     e2e = None
     if not args.no_e2e:
         # host -> device copy of each problem's input, the transform, device ->
-        # host copy of its result; consecutive problems alternate between two
+        # host copy of its result; consecutive problems rotate over a few
         # streams with their own device buffers, so copies overlap transforms
+        nl = max(2, args.e2e_lanes)
         host_in = torch.from_numpy(x_np).pin_memory()
-        host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
-        dbuf = [(xin, yout), (torch.empty_like(xin), torch.empty_like(yout))]
-        lanes = [torch.cuda.Stream(dev) for _ in range(2)]
+        host_out = [torch.empty_like(host_in).pin_memory() for _ in range(nl)]
+        dbuf = [(xin, yout)] + [(torch.empty_like(xin), torch.empty_like(yout)) for _ in range(nl - 1)]
+        lanes = [torch.cuda.Stream(dev) for _ in range(nl)]
         e2e_steps = max(1, min(args.steps, 2))
 
         def e2e_step():
@@ -274,7 +275,7 @@ def run_gpu(args, rank, world):
                 ls.wait_event(fork)
             for i, (label, sign, p, npts, count) in enumerate(plans):
                 m = npts * count
-                ls, (di, do), ho = lanes[i % 2], dbuf[i % 2], host_out[i % 2]
+                ls, (di, do), ho = lanes[i % nl], dbuf[i % nl], host_out[i % nl]
                 with torch.cuda.stream(ls):
                     di[:m].copy_(host_in[:m], non_blocking=True)
                     gbfft.fft_execute(p.handle, di.data_ptr(), do.data_ptr(), ls.cuda_stream)
@@ -322,7 +323,8 @@ def run_gpu(args, rank, world):
         e2e_gbs = 2 * nbytes / (e2e_ms * 1e-3) / 1e9
         e2e = {"value": round(aggregate_gflops(world, step_flops, e2e_ms), 2), "unit": "GFLOP/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": round(e2e_ms, 3),
-               "pipeline": "two streams, copies of one problem overlap the transform of the other",
+               "pipeline": "%d streams in rotation, copies of one problem overlap the transforms of the "
+                           "others" % nl,
                "host_link": {"achieved_gbs": round(e2e_gbs, 1), "peak_gbs": round(link_gbs, 1),
                              "frac": round(e2e_gbs / link_gbs, 3),
                              "peak_kind": "measured here: concurrent pinned H2D + D2H copies of %d bytes each "
@@ -584,6 +586,7 @@ def main():
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
     ap.add_argument("--estimate", action="store_true", help="plan with FFT_ESTIMATE instead of measuring")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-lanes", type=int, default=2, help="e2e: streams the problems rotate over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()
