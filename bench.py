@@ -235,7 +235,7 @@ def run_gpu(args, rank, world):
     # per-plan breakdown; the roofline is taken for the kernel family with the
     # largest share of the step (plans whose passes all use that family)
     per = []
-    fam_bytes, fam_ms = {}, {}
+    fam_alg, fam_pass, fam_ms, fam_launch = {}, {}, {}, {}
     for i, (label, sign, p, npts, count) in enumerate(plans):
         ms = statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
         launches = p.launches
@@ -245,12 +245,25 @@ def run_gpu(args, rank, world):
         per.append({"problem": label, "sign": sign, "ms": round(ms, 4),
                     "gflops": round(flops_of(npts, count) / (ms * 1e-3) / 1e9, 1),
                     "gbs_algorithmic": round(alg / (ms * 1e-3) / 1e9, 1), "launches": launches, "kernels": fam})
-        fam_bytes[fam] = fam_bytes.get(fam, 0.0) + alg * launches
+        fam_alg[fam] = fam_alg.get(fam, 0.0) + alg
+        fam_pass[fam] = fam_pass.get(fam, 0.0) + alg * launches
         fam_ms[fam] = fam_ms.get(fam, 0.0) + ms
+        fam_launch[fam] = fam_launch.get(fam, []) + [(launches, npts * count)]
     dom = max(fam_ms, key=lambda f: fam_ms[f])
     peak, peak_kind = peaks()
-    achieved = fam_bytes[dom] / (fam_ms[dom] * 1e-3) / 1e9
+    # algorithmic bytes: 16 B per point per TRANSFORM (read once, written once);
+    # the scratch round trips of multi-pass plans are not algorithmic
+    achieved = fam_alg[dom] / (fam_ms[dom] * 1e-3) / 1e9
+    pass_achieved = fam_pass[dom] / (fam_ms[dom] * 1e-3) / 1e9
     traffic = recorded_traffic()
+    traffic_exec = None
+    if traffic:
+        # DRAM bytes of one execution of the family's average plan: its launches
+        # times the recorded bytes of one pass, scaled to the plan's points
+        per_pt = traffic["dram_bytes_per_launch"] / float(traffic.get("points", 2 ** 26))
+        runs = fam_launch[dom]
+        traffic_exec = sum(nl * per_pt * pts for nl, pts in runs) / len(runs)
+        alg_exec = sum(16.0 * pts for _, pts in runs) / len(runs)
     kernel_names = {"p2-tma": "gb_p2_kernel / gb_p2small_kernel (TMA power-of-two passes)",
                     "cluster": "gb_cluster_kernel (one pass over a thread-block cluster)",
                     "stockham": "gb_stockham_kernel (generic pass)"}
@@ -342,13 +355,20 @@ def run_gpu(args, rank, world):
                    "step_bytes_algorithmic": step_bytes, "step_flops": step_flops},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
-                     "traffic_launch": (traffic["launch"] if traffic else None),
+                     "traffic": (round(traffic_exec) if traffic_exec else None),
+                     "traffic_over_algorithmic": (round(traffic_exec / alg_exec, 3) if traffic_exec else None),
+                     "traffic_basis": ("DRAM bytes of one execution (all its launches) of the family's average "
+                                       "plan: launches x the ncu bytes of one recorded pass (%s), scaled by points"
+                                       % traffic["launch"]) if traffic else None,
                      "kernel": kernel_names.get(dom, dom),
                      "time_share": round(fam_ms[dom] / sum(fam_ms.values()), 4),
-                     "unit_of_work": "16 B per point per pass (each pass reads and writes every point once)",
-                     "peak_kind": f"{peak_kind} hbm_gbs",
-                     "transform_frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
+                     "unit_of_work": "16 B per point per transform (read once, written once; scratch round "
+                                     "trips of multi-pass plans are not algorithmic)",
+                     "peak_kind": f"{peak_kind} hbm_gbs (of measured)" if peak_kind == "measured"
+                                  else f"{peak_kind} hbm_gbs",
+                     "pass_achieved": round(pass_achieved, 1),
+                     "pass_frac": round(pass_achieved / peak, 4),
+                     "step_frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
         "clocks": clk, "gpu_launches": launches, "plan_seconds": round(plan_s, 2),
         "e2e": e2e, "per_problem": per,
     }
