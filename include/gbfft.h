@@ -160,6 +160,47 @@ int fft_plan_launches(fft_plan p);
  * caller's work area; excludes twiddle tables. */
 size_t fft_plan_scratch_bytes(fft_plan p);
 
+/* ---------------------------------------------------------------- tables */
+
+/*
+ * Twiddle and chirp tables (sec. 6: the accuracy of the transform rests on
+ * twiddle factors computed to about machine precision from an exactly
+ * reduced exponent; sec. 4.2.5: Bluestein's chirp, Rader's permutation).
+ * These two calls expose, for checking, what the planner computes for one
+ * table: fft_twiddle_exponents evaluates on the host the same inline integer
+ * code the device generators run (gb_index.h) and writes the exponent of
+ * every entry; fft_twiddle_table runs the device generator itself.  An entry
+ * with exponent m holds w_N^m = exp(-2 pi i m / N) rounded once from FP64 to
+ * FP32 (the chirp: exp(-pi i m / N); exponent -1: the entry is 1).
+ *   FFT_TABLE_ROOTS      entry i: (i a) mod N, any count (a >= 0)
+ *   FFT_TABLE_STAGE      power-of-two stage table of (L, R) = (a, b): entry
+ *                        4k + t: (2^t k N/(L R)) mod N, -1 where 2^t >= R;
+ *                        count = 4 L
+ *   FFT_TABLE_FULL_STAGE mixed-radix stage table, L = a, R = b, N = L R:
+ *                        entry k W + r - 1 (W = R-1 rounded up to even):
+ *                        (r k) mod N, -1 for r = R; count = L W
+ *   FFT_TABLE_POSTTW     four-step twiddle w_N^{c k} of eq. (2), L = a,
+ *                        columns c < b: entries c L + j: (c j) mod N, then
+ *                        entries b L + 4c + t: (c L 2^t) mod N; count = b (L+4)
+ *   FFT_TABLE_CHIRP      entry k: k^2 mod 2N, count = N
+ *   FFT_TABLE_RADER      entry i: a^i mod N (exponents only; a a generator of
+ *                        the prime N); any count
+ * Arguments: N <= 2^31; out is a host int64_t array that receives the
+ * exponents of the first `count` entries (count <= the table's size), or a
+ * device complex64 array that receives the whole table (count = its size;
+ * `stream` a cudaStream_t, the call only enqueues).
+ * Returns FFT_OK, FFT_ERR_INVALID_ARG (kind, sizes or count inconsistent) or
+ * FFT_ERR_CUDA.
+ */
+#define FFT_TABLE_ROOTS 0
+#define FFT_TABLE_STAGE 1
+#define FFT_TABLE_FULL_STAGE 2
+#define FFT_TABLE_POSTTW 3
+#define FFT_TABLE_CHIRP 4
+#define FFT_TABLE_RADER 5
+int fft_twiddle_exponents(int kind, int64_t N, int64_t a, int64_t b, int64_t count, int64_t *out);
+int fft_twiddle_table(int kind, int64_t N, int64_t a, int64_t b, int64_t count, void *out, void *stream);
+
 /* ---------------------------------------------------------------- wisdom */
 
 /*

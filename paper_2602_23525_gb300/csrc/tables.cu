@@ -8,6 +8,7 @@
 // rounded once to FP32.  FP64 is used for nothing else on the device.
 #include <cuda_runtime.h>
 
+#include "gb_index.h"
 #include "gb_kernels.h"
 
 namespace {
@@ -16,7 +17,7 @@ namespace {
 __global__ void gb_roots_kernel(float2* out, int64_t count, int64_t N, int64_t mult) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-    const int64_t m = (int64_t)(((unsigned long long)i * (unsigned long long)mult) % (unsigned long long)N);
+    const int64_t m = gb_exp_root(i, N, mult);
     double s, c;
     sincospi(2.0 * (double)m / (double)N, &s, &c);
     out[i] = make_float2((float)c, (float)(-s));
@@ -26,14 +27,11 @@ __global__ void gb_roots_kernel(float2* out, int64_t count, int64_t N, int64_t m
 // per-stage table [k][4]: w_N^{(p k step) mod N} for p = 1, 2, 4, 8, step = N/(L R)
 __global__ void gb_stage_tw_kernel(float2* out, int64_t N, int64_t L, int R) {
   const int64_t total = L * 4;
-  const int64_t step = N / (L * R);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int64_t k = i >> 2;
-    const int64_t r = (int64_t)1 << (i & 3);
+    const int64_t m = gb_exp_stage(i, N, L, R);
     float2 w = make_float2(1.f, 0.f);
-    if (r < R) {
-      const int64_t m = (int64_t)(((unsigned long long)(r * k) * (unsigned long long)step) % (unsigned long long)N);
+    if (m >= 0) {
       double s, c;
       sincospi(2.0 * (double)m / (double)N, &s, &c);
       w = make_float2((float)c, (float)(-s));
@@ -53,12 +51,10 @@ __global__ void gb_posttw_kernel(float2* A, float2* B, int64_t N, int64_t ncols,
   const int64_t na = ncols * L;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + ncols * 4; i += stride) {
     if (i < na) {
-      const int64_t c = i / L, j = i - (i / L) * L;
-      A[i] = root64((int64_t)(((unsigned long long)c * (unsigned long long)j) % (unsigned long long)N), N);
+      A[i] = root64(gb_exp_posttw_a(i, N, L), N);
     } else {
-      const int64_t q = i - na, c = q >> 2, p = (int64_t)1 << (q & 3);
-      const unsigned long long e = ((unsigned long long)c * (unsigned long long)(L * p)) % (unsigned long long)N;
-      B[q] = root64((int64_t)e, N);
+      const int64_t q = i - na;
+      B[q] = root64(gb_exp_posttw_b(q, N, L), N);
     }
   }
 }
@@ -71,8 +67,8 @@ __global__ void gb_full_stage_tw_kernel(float2* out, int64_t L, int R) {
   const int64_t N = L * R;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int64_t k = i / W, r = i - k * W + 1;
-    out[i] = r < R ? root64((int64_t)(((unsigned long long)(r * k)) % (unsigned long long)N), N) : make_float2(1.f, 0.f);
+    const int64_t m = gb_exp_full_stage(i, L, R);
+    out[i] = m >= 0 ? root64(m, N) : make_float2(1.f, 0.f);
   }
 }
 
@@ -80,7 +76,7 @@ __global__ void gb_full_stage_tw_kernel(float2* out, int64_t L, int R) {
 __global__ void gb_chirp_kernel(float2* out, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-    const int64_t q = (int64_t)(((unsigned long long)k * (unsigned long long)k) % (unsigned long long)(2 * n));
+    const int64_t q = gb_exp_chirp(k, n);
     double s, c;
     sincospi((double)q / (double)n, &s, &c);
     out[k] = make_float2((float)c, (float)(-s));
@@ -96,7 +92,7 @@ __global__ void gb_blue_b_kernel(double2* b, int64_t n, int64_t m) {
     else if (i > m - n) j = m - i;
     double2 v = make_double2(0.0, 0.0);
     if (j >= 0) {
-      const int64_t q = (int64_t)(((unsigned long long)j * (unsigned long long)j) % (unsigned long long)(2 * n));
+      const int64_t q = gb_exp_chirp(j, n);
       double s, c;
       sincospi((double)q / (double)n, &s, &c);
       v = make_double2(c, s);  // conj(exp(-pi i q / n))
@@ -119,7 +115,7 @@ __global__ void gb_fft64_stage_kernel(const double2* x, double2* y, int64_t m, i
     const int64_t f = k + t * L;
     double2 acc = make_double2(0.0, 0.0);
     for (int r = 0; r < R; ++r) {
-      const int64_t e = ((int64_t)r * f) % LR;
+      const int64_t e = gb_mulmod(r, f, LR);
       double s, c;
       sincospi(2.0 * (double)e / (double)LR, &s, &c);
       const double2 v = x[j + (int64_t)r * (m / R)];
@@ -191,4 +187,78 @@ cudaError_t gb_make_bluestein_kernel(float2* out, int64_t n, int64_t m, const in
   }
   gb_scale_to_f32_kernel<<<grid_for(m), 256, 0, st>>>(x, out, m, 1.0 / (double)m);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- diagnostics
+// The exponent and value of every entry of one table, computed by the same
+// code the planner runs, for checking against exact integer arithmetic and
+// an FP64 evaluation on the host.
+
+#include "gb_plan.hpp"
+
+namespace {
+
+// exponent of entry i of a table of the given kind (-1: the entry is 1)
+int64_t table_exponent(int kind, int64_t N, int64_t a, int64_t b, int64_t i) {
+  switch (kind) {
+    case FFT_TABLE_ROOTS: return gb_exp_root(i, N, a);
+    case FFT_TABLE_STAGE: return gb_exp_stage(i, N, a, (int)b);
+    case FFT_TABLE_FULL_STAGE: return gb_exp_full_stage(i, a, (int)b);
+    case FFT_TABLE_POSTTW: return i < a * b ? gb_exp_posttw_a(i, N, a) : gb_exp_posttw_b(i - a * b, N, a);
+    case FFT_TABLE_CHIRP: return gb_exp_chirp(i, N);
+    case FFT_TABLE_RADER: return gb_powmod(a, i, N);
+    default: return -2;
+  }
+}
+
+// arguments of a table: its size, or -1 when they do not describe one
+int64_t table_size(int kind, int64_t N, int64_t a, int64_t b) {
+  const int64_t lim = (int64_t)1 << 31;
+  if (N < 1 || N > lim) return -1;
+  switch (kind) {
+    case FFT_TABLE_ROOTS: return a >= 0 ? -2 : -1;  // any count
+    case FFT_TABLE_STAGE:
+      return (a >= 1 && b >= 2 && b <= 16 && N % (a * b) == 0) ? 4 * a : -1;
+    case FFT_TABLE_FULL_STAGE:
+      return (a >= 1 && b >= 2 && b <= 64 && N == a * b) ? a * (b & ~1) : -1;
+    case FFT_TABLE_POSTTW: return (a >= 1 && b >= 1 && a * b <= lim) ? b * (a + 4) : -1;
+    case FFT_TABLE_CHIRP: return N;  // 2N <= 2^32 keeps k^2 mod 2N exact
+    case FFT_TABLE_RADER: return (a >= 1 && a < N) ? -2 : -1;
+    default: return -1;
+  }
+}
+
+}  // namespace
+
+extern "C" int fft_twiddle_exponents(int kind, int64_t N, int64_t a, int64_t b, int64_t count, int64_t* out) {
+  // the first `count` entries of the table (count <= its size)
+  const int64_t sz = table_size(kind, N, a, b);
+  if (sz == -1 || count < 0 || (sz >= 0 && count > sz) || (count > 0 && !out))
+    return gb::set_err(FFT_ERR_INVALID_ARG);
+  for (int64_t i = 0; i < count; ++i) out[i] = table_exponent(kind, N, a, b, i);
+  return gb::set_err(FFT_OK);
+}
+
+extern "C" int fft_twiddle_table(int kind, int64_t N, int64_t a, int64_t b, int64_t count, void* dev_out,
+                                 void* stream) {
+  const int64_t sz = table_size(kind, N, a, b);
+  if (kind == FFT_TABLE_RADER || sz == -1 || count < 0 || (sz >= 0 && count != sz) || (count > 0 && !dev_out))
+    return gb::set_err(FFT_ERR_INVALID_ARG);
+  if (count == 0) return gb::set_err(FFT_OK);
+  float2* o = (float2*)dev_out;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  switch (kind) {
+    case FFT_TABLE_ROOTS: e = gb_make_roots(o, count, N, a, st); break;
+    case FFT_TABLE_STAGE: e = gb_make_stage_twiddles(o, N, a, (int)b, st); break;
+    case FFT_TABLE_FULL_STAGE: e = gb_make_full_stage_twiddles(o, a, (int)b, st); break;
+    case FFT_TABLE_POSTTW: e = gb_make_posttw(o, o + a * b, N, b, a, st); break;
+    case FFT_TABLE_CHIRP: e = gb_make_chirp(o, N, st); break;
+    default: return gb::set_err(FFT_ERR_INVALID_ARG);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return gb::set_err(FFT_ERR_CUDA);
+  }
+  return gb::set_err(FFT_OK);
 }

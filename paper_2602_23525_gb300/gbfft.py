@@ -40,6 +40,12 @@ FFT_PREC_TC_FP16 = 1 << 4
 FFT_PREC_TC_BF16 = 1 << 5
 FFT_PREC_SPLIT = 1 << 6
 FFT_GROUP_DEBUG_STALL = 1 << 8
+FFT_TABLE_ROOTS = 0
+FFT_TABLE_STAGE = 1
+FFT_TABLE_FULL_STAGE = 2
+FFT_TABLE_POSTTW = 3
+FFT_TABLE_CHIRP = 4
+FFT_TABLE_RADER = 5
 FFT_GROUP_PERSISTENT = 1 << 9
 FFT_GROUP_GRAPH = 1 << 10
 
@@ -95,6 +101,10 @@ _SIGNATURES = {
     "fft_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "fft_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "fft_server_destroy": (None, [ctypes.c_void_p]),
+    "fft_twiddle_exponents": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_void_p]),
+    "fft_twiddle_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "fft_execute_1d_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -298,6 +308,26 @@ def fft_server_stats(server) -> dict:
 def fft_server_destroy(server) -> None:
     if server:
         load().fft_server_destroy(server)
+
+
+def fft_twiddle_exponents(kind: int, N: int, a: int, b: int, count: int):
+    """Exponent of every entry of one twiddle / chirp table (host evaluation of
+    the generators' integer code); returns a numpy int64 array."""
+    import numpy as np
+    out = np.empty(max(0, int(count)), dtype=np.int64)
+    rc = load().fft_twiddle_exponents(int(kind), int(N), int(a), int(b), int(count),
+                                      ctypes.c_void_p(out.ctypes.data if count else 0))
+    if rc != FFT_OK:
+        raise GbfftError(rc, "fft_twiddle_exponents")
+    return out
+
+
+def fft_twiddle_table(kind: int, N: int, a: int, b: int, count: int, out_ptr: int, stream: int = 0) -> None:
+    """Run the device generator of one table into a complex64 device array."""
+    rc = load().fft_twiddle_table(int(kind), int(N), int(a), int(b), int(count), ctypes.c_void_p(out_ptr),
+                                  ctypes.c_void_p(stream))
+    if rc != FFT_OK:
+        raise GbfftError(rc, "fft_twiddle_table")
 
 
 def fft_execute_1d_noalloc(n: int, batch: int, sign: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
