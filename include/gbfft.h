@@ -73,7 +73,13 @@ enum {
 #define FFT_EXTERNAL_SCRATCH (1u << 3) /* no plan-owned scratch: pass a work area to fft_execute_scratch */
 #define FFT_PREC_TC_FP16 (1u << 4) /* radix-16 stages as FP16 tensor-core MMAs */
 #define FFT_PREC_TC_BF16 (1u << 5) /* radix-16 stages as BF16 tensor-core MMAs */
-#define FFT_PREC_SPLIT (1u << 6)   /* with a TC flag: split hi+lo operands */
+#define FFT_PREC_SPLIT (1u << 6)   /* with a TC flag: split operands (FP16 hi+lo, BF16 hi+mid+lo) */
+/* Testing only: the plan's first step is one device wait, bounded at 50 ms,
+ * on an mbarrier nothing arrives on.  It runs out and records
+ * FFT_ERR_DEVICE_TIMEOUT in the plan's status word exactly as a kernel whose
+ * tile copy never landed would (see fft_sync_status); nothing faults and the
+ * transform itself still runs. */
+#define FFT_DEBUG_STALL (1u << 11)
 
 /* ---------------------------------------------------------------- plans */
 
@@ -106,9 +112,24 @@ fft_plan fft_plan_dft(int rank, const fft_iodim *dims, int howmany_rank,
  *   stream  : a cudaStream_t (NULL = legacy default stream); the call only
  *             enqueues work and returns.
  * Returns FFT_OK or an error code (INVALID_ARG, ALIAS, INPLACE_MISMATCH,
- * CUDA); also reported by fft_last_error().
+ * CUDA); also reported by fft_last_error().  If an earlier execution of the
+ * plan has left a device-side error in its status word that nobody collected
+ * (visible to the host without synchronising, once that kernel has run), the
+ * call returns it (FFT_ERR_DEVICE_TIMEOUT), clears it and enqueues nothing.
  */
 int fft_execute(fft_plan p, const void *in, void *out, void *stream);
+
+/*
+ * fft_sync_status -- wait for the plan's last execution (the last
+ * fft_execute / fft_execute_scratch not made during a stream capture) and
+ * return its device-side status: FFT_OK, or FFT_ERR_DEVICE_TIMEOUT when one
+ * of its kernels' bounded waits gave up (a tile copy or an MMA that did not
+ * complete within 2 s); the status is cleared.  Every wait in the library's
+ * kernels is bounded, so a stuck copy turns into this error, not a hang.
+ * The status word is page-locked host memory mapped into the device.  Returns
+ * FFT_ERR_INVALID_ARG for NULL and FFT_ERR_CUDA if the wait itself failed.
+ */
+int fft_sync_status(fft_plan p);
 
 /*
  * fft_execute_scratch -- run a plan made with FFT_EXTERNAL_SCRATCH, using the

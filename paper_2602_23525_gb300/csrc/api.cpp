@@ -93,14 +93,19 @@ int fft_plan_explain(int rank, const fft_iodim* dims, int howmany_rank, const ff
 int fft_execute(fft_plan p, const void* in, void* out, void* stream) {
   if (!p) return set_err(FFT_ERR_INVALID_ARG);
   if (p->d.external_scratch && !p->d.scratch.empty()) return set_err(FFT_ERR_INVALID_ARG);
-  const int rc = execute_plan(&p->d, in, out, (cudaStream_t)stream);
+  const int rc = execute_plan(&p->d, in, out, (cudaStream_t)stream, nullptr, true);
   return set_err(rc);
 }
 
 int fft_execute_scratch(fft_plan p, const void* in, void* out, void* scratch, void* stream) {
   if (!p) return set_err(FFT_ERR_INVALID_ARG);
   if (!p->d.external_scratch) return set_err(FFT_ERR_INVALID_ARG);
-  return set_err(execute_plan(&p->d, in, out, (cudaStream_t)stream, scratch));
+  return set_err(execute_plan(&p->d, in, out, (cudaStream_t)stream, scratch, true));
+}
+
+int fft_sync_status(fft_plan p) {
+  if (!p) return set_err(FFT_ERR_INVALID_ARG);
+  return set_err(take_status(&p->d, true));
 }
 
 void fft_destroy(fft_plan p) {

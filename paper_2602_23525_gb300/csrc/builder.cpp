@@ -1361,11 +1361,31 @@ static void release(PlanData* p) {
     if (t) cudaFree(t);
   for (void* s : p->scratch)
     if (s) cudaFree(s);
-  if (p->d_status) cudaFree(p->d_status);
+  if (p->h_status) cudaFreeHost(p->h_status);
+  else if (p->d_status) cudaFree(p->d_status);
+  if (p->done) cudaEventDestroy(p->done);
   p->tables.clear();
   p->scratch.clear();
   p->scratch_bytes.clear();
   p->d_status = nullptr;
+  p->h_status = nullptr;
+  p->done = nullptr;
+  p->done_valid = false;
+}
+
+int take_status(PlanData* p, bool wait) {
+  if (!p->d_status) return FFT_OK;
+  if (wait && p->done_valid && cudaEventSynchronize(p->done) != cudaSuccess) return FFT_ERR_CUDA;
+  int v = 0;
+  if (p->h_status) {
+    v = *reinterpret_cast<volatile int*>(p->h_status);
+    if (v) *reinterpret_cast<volatile int*>(p->h_status) = 0;
+  } else {
+    if (!wait) return FFT_OK;  // a device-memory word is read only after a wait
+    if (cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FFT_ERR_CUDA;
+    if (v && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return FFT_ERR_CUDA;
+  }
+  return v;
 }
 
 void free_plan(PlanData* p) { release(p); }
@@ -1420,6 +1440,10 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
     }
     case STEP_BLUE_MUL: {
       e = gb_launch_blue_mul(s.blue, bufs[s.dst], st);
+      break;
+    }
+    case STEP_STALL: {
+      e = gb_launch_stall(s.pass.status, 50000000ull, st);  // 50 ms
       break;
     }
     case STEP_BLUE_POST: {
@@ -1539,17 +1563,42 @@ int build_plan(const Problem& P, bool device, PlanData* out) {
       cudaGetLastError();
       return FFT_ERR_NO_DEVICE;
     }
-    if (cudaMalloc(&out->d_status, sizeof(int)) != cudaSuccess) {
+    // the status word in mapped page-locked memory, so that fft_execute can
+    // see an earlier execution's error without synchronising the device
+    void* hp = nullptr;
+    if (cudaHostAlloc(&hp, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess &&
+        cudaHostGetDevicePointer((void**)&out->d_status, hp, 0) == cudaSuccess) {
+      out->h_status = (int*)hp;
+      *out->h_status = 0;
+    } else {
       cudaGetLastError();
-      return FFT_ERR_OOM;
+      if (hp) cudaFreeHost(hp);
+      out->d_status = nullptr;
+      if (cudaMalloc(&out->d_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return FFT_ERR_OOM;
+      }
+      cudaMemset(out->d_status, 0, sizeof(int));
     }
-    cudaMemset(out->d_status, 0, sizeof(int));
+    if (cudaEventCreateWithFlags(&out->done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      release(out);
+      return FFT_ERR_CUDA;
+    }
   }
   const bool measure = device && !(P.flags & FFT_ESTIMATE);
   Builder b(out, device, measure, (P.flags & FFT_WISDOM_ONLY) != 0);
   if (P.flags & (FFT_PREC_TC_FP16 | FFT_PREC_TC_BF16))
     b.prec = ((P.flags & FFT_PREC_TC_FP16) ? 1 : 2) + ((P.flags & FFT_PREC_SPLIT) ? 2 : 0);
   const int conj = P.sign > 0 ? 1 : 0;
+  if (P.flags & FFT_DEBUG_STALL) {
+    Step st;
+    st.kind = STEP_STALL;
+    st.pass.status = out->d_status;
+    out->steps.push_back(st);
+    b.line(1, "debug stall: one wait on an mbarrier nothing arrives on, bounded at 50 ms (reports "
+              "FFT_ERR_DEVICE_TIMEOUT)");
+  }
   b.solve(P.N, P.V, BUF_IN, out->inplace ? BUF_IN : BUF_OUT, conj, 1);
   if (!b.err && device && cudaStreamSynchronize(0) != cudaSuccess) b.err = FFT_ERR_CUDA;
   out->info = head.str() + b.info.str();
@@ -1575,13 +1624,30 @@ int check_execute_args(const PlanData* p, const void* in, const void* out) {
   return FFT_OK;
 }
 
-int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st, void* work) {
+int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st, void* work, bool api) {
   if (p->prob.empty) return FFT_OK;
   const int rc = check_execute_args(p, in, out);
   if (rc != FFT_OK) return rc;
   if (p->external_scratch && !p->scratch.empty() && (!work || ((uintptr_t)work & 255)))
     return FFT_ERR_INVALID_ARG;
-  return run_steps(p, in, p->inplace ? (void*)in : out, st, work);
+  if (api) {
+    // an error an earlier execution left in the status word (seen without a
+    // device synchronisation) is reported now, and nothing is enqueued
+    const int prev = take_status(p, false);
+    if (prev != FFT_OK) return prev;
+  }
+  const int r = run_steps(p, in, p->inplace ? (void*)in : out, st, work);
+  if (api && r == FFT_OK && p->done) {
+    // the completion event of the last execution (not inside a stream capture,
+    // where a recorded event cannot be waited on from the host)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FFT_ERR_CUDA;
+    if (cs == cudaStreamCaptureStatusNone) {
+      if (cudaEventRecord(p->done, st) != cudaSuccess) return FFT_ERR_CUDA;
+      p->done_valid = true;
+    }
+  }
+  return r;
 }
 
 }  // namespace gb

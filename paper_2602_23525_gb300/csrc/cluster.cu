@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(CL<LOGN1, LOGN2, C, NB>::THREADS, CL<LOGN1, LO
       const uint32_t parity = (uint32_t)((NB == 1 ? it : (it >> 1)) & 1);
       const bool ok = bad ? false : mbar_wait(smem_addr(bars + p), parity);
       if (__syncthreads_or(!ok)) {
-        if (!bad && tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
+        if (!bad && tid == 0 && k.status) gb_set_status(k.status, kStatusTimeout);
         bad = true;
       }
     } else {

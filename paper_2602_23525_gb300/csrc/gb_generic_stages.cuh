@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "codelets.cuh"
+#include "gb_status.cuh"
 #include "gb_kernels.h"
 #include "gb_pass.h"
 #include "gb_pointwise.cuh"
@@ -145,7 +146,7 @@ __device__ __forceinline__ void run_stage(const GbPass& p, int s, float2* sm, co
     case 11: stage<11>(p, s, sm, c, from_g, to_g); break;
     case 13: stage<13>(p, s, sm, c, from_g, to_g); break;
     default:
-      if (threadIdx.x == 0 && p.status) atomicExch(p.status, 2);
+      if (threadIdx.x == 0 && p.status) gb_set_status(p.status, 2);
       break;
   }
 }

@@ -59,6 +59,8 @@ int gb_p2_twiddle_elems(int logn);               // float2 entries of the stage 
 int gb_p2_stage(int logn, int s, int* L, int* R, int* offset);
 int gb_p2_last_L(int logn);
 cudaError_t gb_launch_p2(const GbP2& k, cudaStream_t st);
+// one bounded wait on an mbarrier nothing arrives on; records the timeout code
+cudaError_t gb_launch_stall(int* status, unsigned long long limit_ns, cudaStream_t st);
 // tensor-core variants (tc.cu): 2^12 contiguous tiles, 2^8 contiguous or column tiles
 int gb_tc_supported(int logn, int load, int store, int posttw);
 int gb_tc_tile(int logn, int load, int store);

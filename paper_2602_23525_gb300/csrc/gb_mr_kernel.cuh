@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     if (tma) {
       const bool ok = mbar_wait(smem_addr(bars + b), (uint32_t)((it >> 1) & 1));
       if (__syncthreads_or(!ok)) {
-        if (tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
+        if (tid == 0 && k.status) gb_set_status(k.status, kStatusTimeout);
         return;
       }
     } else {

@@ -43,7 +43,8 @@ enum StepKind {
   STEP_BLUE_POST = 4,
   STEP_POW2 = 5,
   STEP_CLUSTER = 6,
-  STEP_MR = 7
+  STEP_MR = 7,
+  STEP_STALL = 8   // FFT_DEBUG_STALL: a bounded wait that runs out
 };
 
 // Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.
@@ -73,7 +74,12 @@ struct PlanData {
   std::vector<size_t> scratch_bytes;
   std::vector<size_t> scratch_offset;  // external scratch: offsets in the caller's work area
   bool external_scratch = false;
+  // status word: page-locked host memory mapped into the device (h_status,
+  // its device alias d_status), or device memory alone (h_status null)
   int* d_status = nullptr;
+  int* h_status = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after each fft_execute outside stream capture
+  bool done_valid = false;
   std::string info;
   double bytes = 0.0, flops = 0.0;
   int64_t in_lo = 0, in_hi = 0, out_lo = 0, out_hi = 0;
@@ -105,9 +111,15 @@ void wisdom_put(const std::string& key, const std::string& val);
 // text only (no allocation, no timing).  Returns an FFT_* code.
 int build_plan(const Problem& P, bool device, PlanData* out);
 void free_plan(PlanData* p);
-int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st, void* work = nullptr);
+// api: a call of the public entry points (reports an error an earlier
+// execution left, records the completion event); internal callers (groups,
+// the serving loop) pass false
+int execute_plan(PlanData* p, const void* in, void* out, cudaStream_t st, void* work = nullptr, bool api = false);
 int check_execute_args(const PlanData* p, const void* in, const void* out);
 int launch_step(const Step& s, float2* const* bufs, cudaStream_t st);
+// the plan's device-side error code (0 = none), cleared; `wait` first waits
+// for the plan's last execution
+int take_status(PlanData* p, bool wait);
 
 }  // namespace gb
 

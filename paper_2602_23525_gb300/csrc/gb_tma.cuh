@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gb_status.cuh"
+
 namespace {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
@@ -32,13 +34,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait for phase `parity` of the mbarrier at `bar`
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// wait for phase `parity` of the mbarrier at `bar`, giving up after limit_ns
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (!mbar_try(bar, parity))
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   return true;
+}
+
+// bounded wait for phase `parity` of the mbarrier at `bar`
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, kWaitLimitNs);
 }
 
 __device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {

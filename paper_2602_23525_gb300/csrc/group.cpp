@@ -484,17 +484,18 @@ extern "C" int fft_group_status(fft_group g) {
   if (!g) return set_err(FFT_ERR_INVALID_ARG);
   if (cudaDeviceSynchronize() != cudaSuccess) return set_err(FFT_ERR_CUDA);
   int bad = 0;
-  std::vector<int*> words;
-  if (g->dstatus) words.push_back(g->dstatus);
-  for (fft_plan p : g->plans)
-    if (p->d.d_status) words.push_back(p->d.d_status);
-  for (int* w : words) {
+  if (g->dstatus) {
     int v = 0;
-    if (cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return set_err(FFT_ERR_CUDA);
+    if (cudaMemcpy(&v, g->dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return set_err(FFT_ERR_CUDA);
     if (v != 0) {
       bad = 1;
-      cudaMemset(w, 0, sizeof(int));
+      cudaMemset(g->dstatus, 0, sizeof(int));
     }
+  }
+  for (fft_plan p : g->plans) {
+    const int v = take_status(&p->d, true);
+    if (v == FFT_ERR_CUDA) return set_err(FFT_ERR_CUDA);
+    if (v != FFT_OK) bad = 1;
   }
   return set_err(bad ? FFT_ERR_DEVICE_TIMEOUT : FFT_OK);
 }

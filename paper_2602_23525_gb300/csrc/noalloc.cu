@@ -61,6 +61,17 @@ int scratch_address(float2** out) {
   return FFT_OK;
 }
 
+// Writes the two pass descriptors into the static array.  They travel as
+// kernel parameters, so no host buffer has to stay alive and nothing is
+// copied from pageable memory (which would block the calling thread).
+__global__ void gb_noalloc_desc_kernel(GbPass* d1, const __grid_constant__ GbPass p1, GbPass* d2,
+                                       const __grid_constant__ GbPass p2) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *d1 = p1;
+    *d2 = p2;
+  }
+}
+
 bool smooth(int64_t n) { return gb::smooth_codelet(n); }
 
 // n = n1 n2 with both factors codelet-smooth and at most 4096; n1 the largest
@@ -172,9 +183,8 @@ extern "C" int fft_execute_1d_noalloc(int64_t n, int64_t batch, int sign, const 
   p2.ntiles = p2.tiles0 * batch;
   p2.conj = p1.conj;
 
-  if (cudaMemcpyAsync(d1, &p1, sizeof(GbPass), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d2, &p2, sizeof(GbPass), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return set_err(FFT_ERR_CUDA);
+  gb_noalloc_desc_kernel<<<1, 32, 0, st>>>(d1, p1, d2, p2);
+  if (cudaGetLastError() != cudaSuccess) return set_err(FFT_ERR_CUDA);
   const size_t sm1 = (size_t)p1.T * p1.pitch * sizeof(float2);
   const size_t sm2 = (size_t)p2.T * p2.pitch * sizeof(float2);
   if (gb_launch_pass(p1, d1, (const float2*)in, scratch, p1.T * p1.tpt, sm1, 0, st) != cudaSuccess ||

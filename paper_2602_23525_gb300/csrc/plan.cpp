@@ -62,7 +62,7 @@ std::string dims_str(const std::vector<Dim>& v) {
 }
 
 static const unsigned kKnownFlags = FFT_ESTIMATE | FFT_WISDOM_ONLY | FFT_INPLACE | FFT_EXTERNAL_SCRATCH | FFT_PREC_TC_FP16 |
-                                    FFT_PREC_TC_BF16 | FFT_PREC_SPLIT;
+                                    FFT_PREC_TC_BF16 | FFT_PREC_SPLIT | FFT_DEBUG_STALL;
 
 int canonicalize(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, int sign,
                  unsigned flags, Problem& P) {

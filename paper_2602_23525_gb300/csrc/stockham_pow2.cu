@@ -31,8 +31,9 @@
 // across the T transforms, so T adjacent outputs form one segment).
 // With POSTTW the outputs are multiplied by the four-step twiddle
 // w_N^{l2 k1} of eq. (2) (l2 = column, k1 = output index).
-// Every mbarrier wait is bounded by %globaltimer; on timeout the CTA records
-// FFT_ERR_DEVICE_TIMEOUT in the status word and returns.
+// Every mbarrier wait is bounded by %globaltimer; on timeout the CTA waits
+// (bounded) for the copies it has in flight, records FFT_ERR_DEVICE_TIMEOUT
+// in the status word and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -57,6 +58,16 @@ struct GbRowsMap {
   int use;
   int pos;
 };
+
+// After a wait gave up at iteration `it` (tile `tile`): the copies of
+// iterations it .. it + NBUF - 1 were issued into this CTA's shared memory;
+// wait for each (bounded again) before the CTA exits.
+template <int NBUF>
+__device__ __forceinline__ void drain_copies(uint64_t* bars, int it, int64_t tile, int64_t ntiles) {
+  for (int j = 0; j < NBUF; ++j)
+    if (tile + (int64_t)j * gridDim.x < ntiles)
+      mbar_wait(smem_addr(bars + (it + j) % NBUF), (uint32_t)(((it + j) / NBUF) & 1));
+}
 
 // Thread -> (transform t, thread u within the transform):
 //   "j-fast": t = tid / TPT, u = tid % TPT (lanes along a transform)
@@ -154,7 +165,8 @@ __global__ void __launch_bounds__(T*(1 << LOGN) / 16, MINB)
     const uint32_t parity = (uint32_t)((it / NBUF) & 1);
     const bool ok = mbar_wait(smem_addr(bars + b), parity);
     if (__syncthreads_or(!ok)) {
-      if (tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
+      drain_copies<NBUF>(bars, it, tile, ntiles);
+      if (tid == 0 && k.status) gb_set_status(k.status, kStatusTimeout);
       return;
     }
     int64_t ib, ob, c0;
@@ -310,7 +322,8 @@ __global__ void __launch_bounds__(256, 2) gb_p2small_kernel(const __grid_constan
     const int b = it % NBUF;
     const bool ok = mbar_wait(smem_addr(bars + b), (uint32_t)((it / NBUF) & 1));
     if (__syncthreads_or(!ok)) {
-      if (tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
+      drain_copies<NBUF>(bars, it, tile, ntiles);
+      if (tid == 0 && k.status) gb_set_status(k.status, kStatusTimeout);
       return;
     }
     const int64_t c0 = tile * T;
@@ -439,7 +452,28 @@ cudaError_t dispatch(const GbP2& k, cudaStream_t st) {
   return cudaErrorInvalidValue;
 }
 
+// The debug stall of a plan (FFT_DEBUG_STALL): one wait, bounded at
+// limit_ns, on an mbarrier that nothing arrives on.  The wait runs out, the
+// kernel records FFT_ERR_DEVICE_TIMEOUT in the plan's status word exactly
+// as a pass kernel whose tile copy never landed would, and returns; nothing
+// faults and the context stays usable.
+__global__ void gb_stall_kernel(int* status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_for(smem_addr(&bar), 0, limit_ns);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) gb_set_status(status, kStatusTimeout);
+}
+
 }  // namespace
+
+cudaError_t gb_launch_stall(int* status, unsigned long long limit_ns, cudaStream_t st) {
+  gb_stall_kernel<<<1, 32, 0, st>>>(status, limit_ns);
+  return cudaGetLastError();
+}
 
 void* gb_tensor_map_encoder() {
   static std::once_flag once;

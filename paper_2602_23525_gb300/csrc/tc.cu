@@ -14,9 +14,10 @@
 // no swizzle) and reads row `tid` of the result -- TMEM lane tid mod 128 in
 // the column block of M-tile tid / 128 -- with tcgen05.ld.  Twiddles are
 // applied in FP32 before the rounding (table of (w, w^2, w^4, w^8), as in the
-// FP32 kernels).  The split forms write every operand as hi + lo (hi =
-// round(v), lo = round(v - hi)) and accumulate hi*hi + lo*hi + hi*lo:
-// [A_hi | A_lo] . [B_hi ; B_hi] (K = 64) then A_hi . B_lo (K = 32).
+// FP32 kernels).  The split forms write every operand as a sum of rounded
+// components (hi = round(v), lo = round(v - hi), ...): FP16 as hi + lo with
+// the products hi*hi + lo*hi + hi*lo, BF16 as hi + mid + lo with the six
+// products of order down to 2^-16 (struct Prec).
 //
 // Tiles move as in stockham_pow2.cu: copy-engine loads (bulk copies of
 // contiguous transforms, tensor-map boxes of T columns) on an mbarrier into
@@ -24,8 +25,9 @@
 // it; two CTAs per SM hide each other's copy and MMA waits.  Stores are
 // contiguous or column-wise.  Sizes:
 // 2^8 and 2^12 points (all stages radix 16).  Every wait is bounded by
-// %globaltimer; a CTA whose wait gives up records FFT_ERR_DEVICE_TIMEOUT and
-// leaves the tile loop, and always frees its tensor memory.
+// %globaltimer; a CTA whose wait gives up records FFT_ERR_DEVICE_TIMEOUT,
+// leaves the tile loop, waits (bounded) for the MMA and the tile copy it had
+// in flight, and always frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -57,13 +59,29 @@ struct TC {
   }
 };
 
-// operand precision: PREC 1/3 = FP16, 2/4 = BF16; 3/4 split into hi + lo
+// operand precision: PREC 1/3 = FP16, 2/4 = BF16.  PREC 3 splits every
+// operand into hi + lo (FP16 keeps 11 bits each, ~22 together) and sums the
+// products hi.hi + lo.hi + hi.lo; PREC 4 splits into hi + mid + lo (BF16 keeps
+// 8 bits each, ~24 together: the FP32 mantissa) and sums the six products
+// whose order is at most 2^-16: hi.hi, mid.hi, lo.hi, hi.mid, mid.mid, hi.lo.
+// Each product is a K = 32 block; A holds NC components side by side, B one
+// block per product (its B component), and K step s of the MMA pairs A
+// component acomp(s/2) with B block s/2.
 template <int PREC>
 struct Prec {
   static constexpr bool split = PREC >= 3;
-  static constexpr int KA = split ? 8 : 4;   // 8-element K chunks per row of A: [hi | lo] or [x]
-  static constexpr int KB = split ? 12 : 4;  // per row of B: [hi | hi | lo] or [F]
+  static constexpr int NC = PREC == 4 ? 3 : (PREC == 3 ? 2 : 1);  // components per operand
+  static constexpr int NP = PREC == 4 ? 6 : (PREC == 3 ? 3 : 1);  // products summed
+  static constexpr int KA = 4 * NC;  // 8-element K chunks per row of A: [hi | mid | lo]
+  static constexpr int KB = 4 * NP;  // per row of B: one K = 32 block per product
   static constexpr uint32_t fmt = (PREC == 1 || PREC == 3) ? 0u : 1u;  // F16 0, BF16 1
+  // (A component, B component) of product p
+  __host__ __device__ static constexpr int acomp(int p) {
+    return NP == 6 ? (p < 3 ? p : (p == 4 ? 1 : 0)) : (NP == 3 ? (p == 1 ? 1 : 0) : 0);
+  }
+  __host__ __device__ static constexpr int bcomp(int p) {
+    return NP == 6 ? (p < 3 ? 0 : (p < 5 ? 1 : 2)) : (NP == 3 ? (p == 2 ? 1 : 0) : 0);
+  }
 };
 
 template <int PREC>
@@ -88,11 +106,17 @@ __device__ __forceinline__ float2 unpack(uint32_t u) {
   }
 }
 
+// (a, b) as NC packed components: c[0] = round(a, b), c[i] = round(residual
+// after c[0..i-1]); the residuals are exact in FP32
 template <int PREC>
-__device__ __forceinline__ void pack_split(float a, float b, uint32_t* hi, uint32_t* lo) {
-  *hi = pack<PREC>(a, b);
-  const float2 h = unpack<PREC>(*hi);
-  *lo = pack<PREC>(a - h.x, b - h.y);
+__device__ __forceinline__ void pack_split(float a, float b, uint32_t* c) {
+#pragma unroll
+  for (int i = 0; i < Prec<PREC>::NC; ++i) {
+    c[i] = pack<PREC>(a, b);
+    const float2 h = unpack<PREC>(c[i]);
+    a -= h.x;
+    b -= h.y;
+  }
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -137,30 +161,30 @@ __device__ __forceinline__ void twiddle16(float2* v, const float4* tw) {
   for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], p[r]);
 }
 
-// row `row` of A: points 0..15 re (chunks 0, 1), im (chunks 2, 3); split:
-// hi (0..3), lo (4..7)
+// row `row` of A: points 0..15 re (chunks 0, 1), im (chunks 2, 3) of each
+// component (component i at chunks 4i .. 4i+3)
 template <int PREC>
 __device__ __forceinline__ void write_row(uint32_t abase, int row, const float2* x) {
   using P = Prec<PREC>;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int r0 = (c & 1) * 8;
-    uint32_t h[4], l[4];
+    uint32_t h[4][P::NC];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float a = (c < 2) ? x[r0 + 2 * i].x : x[r0 + 2 * i].y;
       const float b = (c < 2) ? x[r0 + 2 * i + 1].x : x[r0 + 2 * i + 1].y;
-      if constexpr (P::split) pack_split<PREC>(a, b, &h[i], &l[i]);
-      else h[i] = pack<PREC>(a, b);
+      pack_split<PREC>(a, b, h[i]);
     }
-    st_shared_v4(abase + core_off(row, c, P::KA), h[0], h[1], h[2], h[3]);
-    if constexpr (P::split) st_shared_v4(abase + core_off(row, 4 + c, P::KA), l[0], l[1], l[2], l[3]);
+#pragma unroll
+    for (int q = 0; q < P::NC; ++q)
+      st_shared_v4(abase + core_off(row, 4 * q + c, P::KA), h[0][q], h[1][q], h[2][q], h[3][q]);
   }
 }
 
 // B^T (rows n = output re 0..15 then im 0..15, K = points re then im):
 // n < 16:  [C(nr) | -S(nr)],  n >= 16: [S(qr) | C(qr)] with q = n - 16;
-// split: [hi | hi | lo]
+// block p (chunks 4p .. 4p+3) holds component bcomp(p)
 template <int PREC>
 __device__ void build_b(uint32_t bbase, int tid) {
   using P = Prec<PREC>;
@@ -168,7 +192,7 @@ __device__ void build_b(uint32_t bbase, int tid) {
   const int n = tid, q = n & 15;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    uint32_t h[4], l[4];
+    uint32_t h[4][P::NC];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       float v2[2];
@@ -179,19 +203,19 @@ __device__ void build_b(uint32_t bbase, int tid) {
         const bool kim = k >= 16;
         v2[e] = n < 16 ? (kim ? -S16[m] : C16[m]) : (kim ? C16[m] : S16[m]);
       }
-      if constexpr (P::split) pack_split<PREC>(v2[0], v2[1], &h[i], &l[i]);
-      else h[i] = pack<PREC>(v2[0], v2[1]);
+      pack_split<PREC>(v2[0], v2[1], h[i]);
     }
-    st_shared_v4(bbase + core_off(n, c, P::KB), h[0], h[1], h[2], h[3]);
-    if constexpr (P::split) {
-      st_shared_v4(bbase + core_off(n, 4 + c, P::KB), h[0], h[1], h[2], h[3]);
-      st_shared_v4(bbase + core_off(n, 8 + c, P::KB), l[0], l[1], l[2], l[3]);
+#pragma unroll
+    for (int p = 0; p < P::NP; ++p) {
+      const int q2 = P::bcomp(p);
+      st_shared_v4(bbase + core_off(n, 4 * p + c, P::KB), h[0][q2], h[1][q2], h[2][q2], h[3][q2]);
     }
   }
 }
 
 // D (TMEM, 2 M-tiles x 32 columns) = A . B for the 256 rows of A; the split
-// forms run K steps over [A_hi | A_lo] . [B_hi ; B_hi] and then A_hi . B_lo
+// forms accumulate one K = 32 block per product (A component acomp(p) times
+// B block p)
 template <int PREC>
 __device__ __forceinline__ void issue_mma(uint32_t tmem, uint32_t abase, uint32_t bbase, uint32_t bar) {
   using P = Prec<PREC>;
@@ -201,7 +225,7 @@ __device__ __forceinline__ void issue_mma(uint32_t tmem, uint32_t abase, uint32_
   for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
     for (int s = 0; s < KSTEPS; ++s) {
-      const int sa = s < P::KA / 2 ? s : s - P::KA / 2;  // A chunks: steps past A's end reuse A_hi
+      const int sa = 2 * P::acomp(s / 2) + (s & 1);  // A's K step within its component
       const uint64_t ad = smem_desc(abase + (uint32_t)(mt * 16 * P::KA * 128 + sa * 256), 128, P::KA * 128);
       const uint64_t bd = smem_desc(bbase + (uint32_t)(s * 256), 128, P::KB * 128);
       asm volatile(
@@ -322,6 +346,10 @@ __global__ void __launch_bounds__(256, 2) gb_tc_kernel(const __grid_constant__ G
   uint32_t mphase = 0;
   bool bad = false;
   int it = 0;
+  // what is in flight, for the exit after a wait gave up: the iteration whose
+  // tile copy was issued and not yet waited for, and an MMA not yet complete
+  int64_t load_it = (int64_t)blockIdx.x < ntiles ? 0 : -1;
+  bool mma_pending = false;
   for (int64_t tile = blockIdx.x; tile < ntiles && !bad; tile += gridDim.x, ++it) {
     const int b = it % NBUF;
     const bool ok = mbar_wait(smem_addr(bars + b), (uint32_t)((it / NBUF) & 1));
@@ -329,6 +357,7 @@ __global__ void __launch_bounds__(256, 2) gb_tc_kernel(const __grid_constant__ G
       bad = true;
       break;
     }
+    load_it = -1;
     int64_t ib, ob, c0, b1, b2;
     origin(tile, &ib, &ob, &c0, &b1, &b2);
     const int64_t cnt = (k.V0 - c0) < T ? (k.V0 - c0) : T;
@@ -356,21 +385,26 @@ __global__ void __launch_bounds__(256, 2) gb_tc_kernel(const __grid_constant__ G
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();  // A written, stage inputs read (tile or exchange rows), previous D read
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (s == 0 && tid < 32) {
-        // the landing buffer is free: refill it with the tile two ahead
+      if (s == 0) {
+        // the landing buffer is free: refill it with the next tile of this CTA
         const int64_t next = tile + (int64_t)NBUF * gridDim.x;
         if (next < ntiles) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          issue(b, next);
+          load_it = it + NBUF;
+          if (tid < 32) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(b, next);
+          }
         }
       }
       if (tid == 0) issue_mma<PREC>(tmem, abase, bbase, mbar);
+      mma_pending = true;
       const bool done = mbar_wait(mbar, mphase);
-      mphase ^= 1;
       if (__syncthreads_or(!done)) {
         bad = true;
         break;
       }
+      mphase ^= 1;
+      mma_pending = false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float2 y[16];
       read_row(tmem, tid, y);
@@ -395,7 +429,13 @@ __global__ void __launch_bounds__(256, 2) gb_tc_kernel(const __grid_constant__ G
       __syncthreads();  // exchange rows written before the next stage reads them
     }
   }
-  if (bad && tid == 0 && k.status) atomicExch(k.status, kStatusTimeout);
+  if (bad) {
+    // a wait gave up: let the MMA and the tile copy already issued land
+    // (each wait bounded again) before tensor and shared memory are released
+    if (mma_pending) mbar_wait(mbar, mphase);
+    if (load_it >= 0) mbar_wait(smem_addr(bars + (int)(load_it % NBUF)), (uint32_t)((load_it / NBUF) & 1));
+    if (tid == 0 && k.status) gb_set_status(k.status, kStatusTimeout);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");

@@ -39,6 +39,7 @@ FFT_EXTERNAL_SCRATCH = 1 << 3
 FFT_PREC_TC_FP16 = 1 << 4
 FFT_PREC_TC_BF16 = 1 << 5
 FFT_PREC_SPLIT = 1 << 6
+FFT_DEBUG_STALL = 1 << 11
 FFT_GROUP_DEBUG_STALL = 1 << 8
 FFT_TABLE_ROOTS = 0
 FFT_TABLE_STAGE = 1
@@ -69,6 +70,7 @@ _SIGNATURES = {
                                        ctypes.POINTER(fft_iodim), ctypes.c_int, ctypes.c_uint]),
     "fft_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fft_destroy": (None, [ctypes.c_void_p]),
+    "fft_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
     "fft_execute_scratch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p]),
     "fft_last_error": (ctypes.c_int, []),
@@ -177,6 +179,11 @@ def fft_execute_scratch(plan, in_ptr: int, out_ptr: int, scratch_ptr: int, strea
                                     ctypes.c_void_p(scratch_ptr), ctypes.c_void_p(stream))
     if rc != FFT_OK:
         raise GbfftError(rc, "fft_execute_scratch")
+
+
+def fft_sync_status(plan) -> int:
+    """Wait for the plan's last execution; its device status (FFT_OK or the error), cleared."""
+    return load().fft_sync_status(plan)
 
 
 def fft_destroy(plan) -> None:

@@ -58,6 +58,38 @@ def test_two_calls_in_a_row_match_planned_path():
         assert np.all(np.isfinite(err)) and err.max() <= TOL, (n, batch, sign, err.max())
 
 
+def test_in_place_and_the_largest_accepted_size():
+    """in == out is accepted; n * batch = GBFFT_NOALLOC_MAX_POINTS is the largest
+    call (n = 2^21, batch 1: the largest split-twiddle tables, S = 1449)."""
+    n, batch = 1 << 21, 1
+    assert n * batch == gbfft.GBFFT_NOALLOC_MAX_POINTS
+    x = torch.from_numpy(fft_inputs.uniform_c64(n * batch, 710)).cuda()
+    b = planned(x, n, batch, -1)
+    a = noalloc(x, n, batch, -1)
+    assert rel(a, b).max() <= TOL
+    # in place, twice in a row (the second call sees the first call's output)
+    for sign, n, batch in ((-1, 4096, 64), (1, 1000, 33)):
+        x = torch.from_numpy(fft_inputs.uniform_c64(n * batch, 720 + n)).cuda()
+        want = planned(x, n, batch, sign)
+        y = x.clone()
+        for _ in range(2):
+            gbfft.fft_execute_1d_noalloc(n, batch, sign, y.data_ptr(), y.data_ptr(),
+                                         torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        twice = y.cpu().numpy().astype(np.complex128).reshape(batch, n)
+        want2 = planned(torch.from_numpy(want.astype(np.complex64).reshape(-1)).cuda(), n, batch, sign)
+        assert rel(twice, want2).max() <= 4 * TOL
+
+
+def test_matches_the_oracle():
+    import oracle
+    n, batch = 3000, 17
+    x = fft_inputs.uniform_c64(n * batch, 730)
+    a = noalloc(torch.from_numpy(x).cuda(), n, batch, -1)
+    ref = oracle.dft(x, [(n, 1, 1)], [(batch, n, n)], -1).reshape(batch, n)
+    assert rel(a, ref).max() <= TOL
+
+
 def test_sizes_beyond_the_static_array_are_refused():
     n = 4096
     batch = gbfft.GBFFT_NOALLOC_MAX_POINTS // n + 1
