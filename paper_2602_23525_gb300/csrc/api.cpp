@@ -170,6 +170,8 @@ extern "C" int fft_import_wisdom(const char* text) {
       if (atoll(val.c_str() + 6) < 2) return set_err(FFT_ERR_WISDOM);
     } else if (val.rfind("blue:", 0) == 0) {
       if (atoll(val.c_str() + 5) < 3) return set_err(FFT_ERR_WISDOM);
+    } else if (val.rfind("rader:", 0) == 0) {
+      if (atoll(val.c_str() + 6) < 2) return set_err(FFT_ERR_WISDOM);
     } else if (val.rfind("cluster:", 0) == 0) {
       int l1 = 0, l2 = 0, cs = 0, nb = 0, cfg[16][4];
       if (sscanf(val.c_str(), "cluster:%d.%d.%d.%d", &l1, &l2, &cs, &nb) != 4) return set_err(FFT_ERR_WISDOM);

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "gb_index.h"
 #include "gb_plan.hpp"
 
 namespace gb {
@@ -1071,6 +1072,130 @@ struct Builder {
     line(depth + 1, "pointwise Y = w conj(D)");
   }
 
+  // Rader's algorithm (sec. 4.2.5) for a prime length p: the nonzero indices
+  // permuted by powers of a generator g turn the DFT into a cyclic
+  // convolution of length p - 1, evaluated by two forward FFTs of length L
+  // (L = p - 1, or a length >= 2p - 3 with zero padding) around a pointwise
+  // multiply by Bhat = DFT_L(b) / L (rader.cu).
+  static bool is_prime(int64_t n) {
+    if (n < 2) return false;
+    for (int64_t q = 2; q * q <= n; ++q)
+      if (n % q == 0) return false;
+    return true;
+  }
+
+  // the smallest generator of the multiplicative group modulo the prime p
+  static int64_t primitive_root(int64_t p) {
+    std::vector<int64_t> f;
+    int64_t m = p - 1;
+    for (int64_t q = 2; q * q <= m; ++q)
+      if (m % q == 0) {
+        f.push_back(q);
+        while (m % q == 0) m /= q;
+      }
+    if (m > 1) f.push_back(m);
+    for (int64_t g = 2; g < p; ++g) {
+      bool gen = true;
+      for (int64_t q : f) gen = gen && gb_powmod(g, (p - 1) / q, p) != 1;
+      if (gen) return g;
+    }
+    return 1;  // p = 2
+  }
+
+  static bool rader_length_ok(int64_t p, int64_t L) {
+    return is_prime(p) && p > 2 && p < ((int64_t)1 << 30) && (L == p - 1 || L >= 2 * p - 3) &&
+           smooth_codelet(L);
+  }
+
+  void emit_rader(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t L, int depth) {
+    const int64_t p = d.n;
+    if (!rader_length_ok(p, L) || (int)V.size() > GB_MAX_VDIMS) {
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    const int64_t g = primitive_root(p), ginv = gb_powmod(g, p - 2, p);
+    std::ostringstream o;
+    o << "rader p=" << p << " g=" << g << " L=" << L << (L == p - 1 ? " (cyclic convolution of length p-1)"
+                                                                    : " (zero-padded convolution)");
+    line(depth, o.str());
+    // permutations, exact in integers: perm[r] = g^r, qidx[g^{-q}] = q
+    std::vector<int> perm(p - 1), qidx(p, 0);
+    int64_t a = 1, c = 1;
+    for (int64_t r = 0; r < p - 1; ++r) {
+      perm[r] = (int)a;
+      qidx[c] = (int)r;
+      a = gb_mulmod(a, g, p);
+      c = gb_mulmod(c, ginv, p);
+    }
+    int* dperm = (int*)dalloc(sizeof(int) * (p - 1));
+    int* dq = (int*)dalloc(sizeof(int) * p);
+    float2* B = (float2*)dalloc(sizeof(float2) * L);
+    if (device && !err) {
+      if (cudaMemcpy(dperm, perm.data(), sizeof(int) * (p - 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(dq, qidx.data(), sizeof(int) * p, cudaMemcpyHostToDevice) != cudaSuccess) {
+        err = FFT_ERR_CUDA;
+        return;
+      }
+      double2* work = nullptr;  // stream-ordered, as for Bluestein's table
+      if (cudaMallocAsync((void**)&work, sizeof(double2) * 2 * L, 0) != cudaSuccess) {
+        cudaGetLastError();
+        err = FFT_ERR_OOM;
+        return;
+      }
+      const std::vector<int> rad = default_radices(L);
+      if (gb_make_rader_kernel(B, p, ginv, L, rad.data(), (int)rad.size(), work, 0) != cudaSuccess)
+        err = FFT_ERR_CUDA;
+      if (cudaFreeAsync(work, 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) err = FFT_ERR_CUDA;
+    }
+    const int64_t count = prod_n(V);
+    GbRaderIO r;
+    memset(&r, 0, sizeof(r));
+    r.p = p;
+    r.L = L;
+    r.is = d.is;
+    r.os = d.os;
+    r.nv = (int)V.size();
+    for (int i = 0; i < r.nv; ++i) {
+      r.vn[i] = V[i].n;
+      r.vis[i] = V[i].is;
+      r.vos[i] = V[i].os;
+    }
+    r.count = count;
+    r.perm = dperm;
+    r.qidx = dq;
+    r.B = B;
+    r.conj = conj;
+    const int S0 = new_scratch((size_t)count * L * sizeof(float2));
+    const int S1 = new_scratch((size_t)count * L * sizeof(float2));
+    const int SD = new_scratch((size_t)count * 2 * sizeof(float2));
+    Step pre;
+    pre.kind = STEP_RADER_PRE;
+    pre.rader = r;
+    pre.src = src;
+    pre.dst = S0;
+    pre.aux = SD;
+    P->steps.push_back(pre);
+    line(depth + 1, "pointwise a = pad(x[g^r]), x0 kept");
+    solve_rank1({L, 1, 1}, {{count, L, L}}, S0, S1, 0, depth + 1);
+    Step mul;
+    mul.kind = STEP_RADER_MUL;
+    mul.rader = r;
+    mul.src = S1;
+    mul.dst = S1;
+    mul.aux = SD;
+    P->steps.push_back(mul);
+    line(depth + 1, "pointwise dc = A[0], Z = conj(A Bhat)");
+    solve_rank1({L, 1, 1}, {{count, L, L}}, S1, S0, 0, depth + 1);
+    Step post;
+    post.kind = STEP_RADER_POST;
+    post.rader = r;
+    post.src = S0;
+    post.dst = dst;
+    post.aux = SD;
+    P->steps.push_back(post);
+    line(depth + 1, "pointwise Y[0] = x0 + dc, Y[g^-q] = x0 + conj(D[q])");
+  }
+
   // ---------------------------------------------------------------- planner
 
   std::string key_rank1(const Dim& d, const std::vector<Dim>& V, bool inplace) const {
@@ -1196,6 +1321,18 @@ struct Builder {
       }
     }
     if (xpose && measure) c.push_back("xpose");
+    // Rader for a prime length: estimate mode takes it first where p - 1 is
+    // smooth (one FFT of length p - 1 each way, against Bluestein's two of
+    // length >= 2p - 1) unless p is small enough for the one-CTA fused
+    // Bluestein pass (one launch); measure mode times it always, and also the
+    // zero-padded power of two
+    const bool rader = !prec && n > 13 && is_prime(n) && n < ((int64_t)1 << 30);
+    int64_t r2 = 1;
+    while (r2 < 2 * n - 3) r2 <<= 1;
+    const int64_t mb = bluestein_length(n);
+    const bool blue_one_cta = n <= 1024 && single_pass_ok(mb, default_radices(mb));
+    if (rader && smooth_codelet(n - 1) && (measure || (generic_prime(n) < 0 && !blue_one_cta)))
+      c.push_back("rader:" + std::to_string(n - 1));
     if (!smooth_codelet(n) || c.empty()) {
       // the convolution length: the smallest 2^a 3^b 5^c 7^d >= 2n - 1, and
       // (measure mode) the next power of two, whose passes run on the
@@ -1211,6 +1348,7 @@ struct Builder {
         c.push_back("blue:" + std::to_string(m2));
       c.push_back("blue:" + std::to_string(m));
       if (measure && m2 != m) c.push_back("blue:" + std::to_string(m2));
+      if (rader && measure) c.push_back("rader:" + std::to_string(r2));
     }
     std::vector<std::string> u;
     for (const std::string& x : c)
@@ -1311,6 +1449,8 @@ struct Builder {
         return;
       }
       emit_fourstep(d, V, src, dst, conj, n1, depth);
+    } else if (choice.rfind("rader:", 0) == 0) {
+      emit_rader(d, V, src, dst, conj, atoll(choice.c_str() + 6), depth);
     } else if (choice.rfind("blue:", 0) == 0) {
       const int64_t m = atoll(choice.c_str() + 5);
       if (m < 2 * d.n - 1) {
@@ -1440,6 +1580,22 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
     }
     case STEP_BLUE_MUL: {
       e = gb_launch_blue_mul(s.blue, bufs[s.dst], st);
+      break;
+    }
+    case STEP_RADER_PRE: {
+      GbRaderIO r = s.rader;
+      r.in = bufs[s.src];
+      e = gb_launch_rader_pre(r, bufs[s.dst], bufs[s.aux], st);
+      break;
+    }
+    case STEP_RADER_MUL: {
+      e = gb_launch_rader_mul(s.rader, bufs[s.dst], bufs[s.aux], st);
+      break;
+    }
+    case STEP_RADER_POST: {
+      GbRaderIO r = s.rader;
+      r.out = bufs[s.dst];
+      e = gb_launch_rader_post(r, bufs[s.src], bufs[s.aux], st);
       break;
     }
     case STEP_STALL: {

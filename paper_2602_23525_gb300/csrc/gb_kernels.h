@@ -143,6 +143,25 @@ cudaError_t gb_launch_blue_pre(const GbBlueIO& b, cudaStream_t st);     // work 
 cudaError_t gb_launch_blue_mul(const GbBlueIO& b, float2* data, cudaStream_t st);  // data = conj(data Bhat)
 cudaError_t gb_launch_blue_post(const GbBlueIO& b, const float2* data, cudaStream_t st);  // y = w conj(data)
 
+// Rader's algorithm for a prime length p (rader.cu): a cyclic convolution of
+// length p - 1 evaluated by FFTs of length L (p - 1, or >= 2p - 3 padded).
+struct GbRaderIO {
+  const float2* in;     // user input, element 0 (set at execute time)
+  float2* out;          // user output, element 0
+  int64_t p, L;         // prime length, convolution FFT length
+  int64_t is, os;       // transform strides
+  int nv;
+  int64_t vn[GB_MAX_VDIMS], vis[GB_MAX_VDIMS], vos[GB_MAX_VDIMS];
+  int64_t count;        // product of vn
+  const int* perm;      // perm[r] = g^r mod p, r < p - 1
+  const int* qidx;      // qidx[k] = q with g^{-q} = k mod p, 0 < k < p
+  const float2* B;      // Bhat = DFT_L(b) / L, L entries
+  int conj;
+};
+cudaError_t gb_launch_rader_pre(const GbRaderIO& b, float2* work, float2* side, cudaStream_t st);
+cudaError_t gb_launch_rader_mul(const GbRaderIO& b, float2* data, float2* side, cudaStream_t st);
+cudaError_t gb_launch_rader_post(const GbRaderIO& b, const float2* data, const float2* side, cudaStream_t st);
+
 // Persistent executor of several plans in one launch (stockham.cu).  Work
 // items are (segment, tile); a segment is one step of one plan and may wait
 // for the segment holding the previous step of the same plan.
@@ -184,3 +203,7 @@ cudaError_t gb_make_full_stage_twiddles(float2* out, int64_t L, int R, cudaStrea
 cudaError_t gb_make_posttw(float2* A, float2* B, int64_t N, int64_t ncols, int64_t L, cudaStream_t st);
 cudaError_t gb_make_bluestein_kernel(float2* out, int64_t n, int64_t m, const int* radices, int nrad,
                                      double2* work, cudaStream_t st);
+// Rader: Bhat = DFT_L(b) / L in FP64, b[m] = w_p^{ginv^m mod p} extended to L
+// (work: 2 L double2; radices: a factorisation of L)
+cudaError_t gb_make_rader_kernel(float2* out, int64_t p, int64_t ginv, int64_t L, const int* radices, int nrad,
+                                 double2* work, cudaStream_t st);

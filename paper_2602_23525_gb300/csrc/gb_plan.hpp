@@ -44,7 +44,10 @@ enum StepKind {
   STEP_POW2 = 5,
   STEP_CLUSTER = 6,
   STEP_MR = 7,
-  STEP_STALL = 8   // FFT_DEBUG_STALL: a bounded wait that runs out
+  STEP_STALL = 8,  // FFT_DEBUG_STALL: a bounded wait that runs out
+  STEP_RADER_PRE = 9,
+  STEP_RADER_MUL = 10,
+  STEP_RADER_POST = 11
 };
 
 // Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.
@@ -60,7 +63,9 @@ struct Step {
   GbMR mr{};                      // STEP_MR; pass/dpass hold the generic pass (run by the group executor)
   GbCopy copy{};
   GbBlueIO blue{};
+  GbRaderIO rader{};
   int src = BUF_IN, dst = BUF_OUT;
+  int aux = -1;                   // a further buffer id (Rader's per-transform side values)
   int threads = 0;
   size_t smem = 0;
   int64_t grid = 0;

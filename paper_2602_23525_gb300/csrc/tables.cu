@@ -127,6 +127,26 @@ __global__ void gb_fft64_stage_kernel(const double2* x, double2* y, int64_t m, i
   }
 }
 
+// Rader's b, extended to the convolution length L (FP64): for m < p - 1,
+// b[m] = w_p^{ginv^m mod p}; where L > p - 1 the cyclic extension
+// b[L - j] = b[p - 1 - j] for 0 < j < p - 1, zeros between
+__global__ void gb_rader_b_kernel(double2* b, int64_t p, int64_t ginv, int64_t L) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += stride) {
+    int64_t j = -1;
+    if (i < p - 1) j = i;
+    else if (i > L - (p - 1)) j = i - L + (p - 1);
+    double2 v = make_double2(0.0, 0.0);
+    if (j >= 0) {
+      const int64_t e = gb_powmod(ginv, j, p);
+      double s, c;
+      sincospi(2.0 * (double)e / (double)p, &s, &c);
+      v = make_double2(c, -s);
+    }
+    b[i] = v;
+  }
+}
+
 __global__ void gb_scale_to_f32_kernel(const double2* x, float2* y, int64_t m, double scale) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
@@ -186,6 +206,23 @@ cudaError_t gb_make_bluestein_kernel(float2* out, int64_t n, int64_t m, const in
     y = t;
   }
   gb_scale_to_f32_kernel<<<grid_for(m), 256, 0, st>>>(x, out, m, 1.0 / (double)m);
+  return cudaGetLastError();
+}
+
+cudaError_t gb_make_rader_kernel(float2* out, int64_t p, int64_t ginv, int64_t L, const int* radices, int nrad,
+                                 double2* work, cudaStream_t st) {
+  double2* x = work;
+  double2* y = work + L;
+  gb_rader_b_kernel<<<grid_for(L), 256, 0, st>>>(x, p, ginv, L);
+  int64_t Lc = 1;
+  for (int s = 0; s < nrad; ++s) {
+    gb_fft64_stage_kernel<<<grid_for(L), 256, 0, st>>>(x, y, L, radices[s], Lc);
+    Lc *= radices[s];
+    double2* t = x;
+    x = y;
+    y = t;
+  }
+  gb_scale_to_f32_kernel<<<grid_for(L), 256, 0, st>>>(x, out, L, 1.0 / (double)L);
   return cudaGetLastError();
 }
 

@@ -140,6 +140,29 @@ def test_plan_prime_is_bluestein():
     assert "bluestein n=97" in t and "bluestein-fused" in t
 
 
+def test_plan_prime_rader():
+    """Rader (sec. 4.2.5) where p - 1 is smooth and p is beyond the one-CTA
+    Bluestein pass; a wisdom entry can force it, padded or not, for any prime."""
+    for p in (1153, 7681, 12289, 65537):
+        t = explain([(p, 1, 1)], [(8, p, p)])
+        assert f"rader p={p}" in t and f"L={p - 1}" in t, t
+        assert t.count("pointwise") == 3
+    t = explain([(10007, 1, 1)], [(8, 10007, 10007)])  # 10006 = 2 x 5003: Bluestein
+    assert "bluestein" in t and "rader" not in t
+    gbfft.fft_forget_wisdom()
+    try:
+        gbfft.fft_import_wisdom("gbfft-wisdom 1\nr1 n=10007 is=1 os=1 v=[(8,10007,10007)] ip=0\trader:32768\n")
+        t = explain([(10007, 1, 1)], [(8, 10007, 10007)])
+        assert "rader p=10007 g=5 L=32768 (zero-padded" in t
+        # a convolution length Rader cannot use is a wisdom error at plan time
+        gbfft.fft_import_wisdom("gbfft-wisdom 1\nr1 n=10007 is=1 os=1 v=[(8,10007,10007)] ip=0\trader:16384\n")
+        with pytest.raises(gbfft.GbfftError) as e:
+            explain([(10007, 1, 1)], [(8, 10007, 10007)])
+        assert e.value.code == gbfft.FFT_ERR_WISDOM
+    finally:
+        gbfft.fft_forget_wisdom()
+
+
 def test_plan_multidim_separable():
     """Rank 2 is one rank-1 problem per dimension (sec. 4.2): the rows in one
     pass, the 4096-long columns as a four-step whose scratch keeps the columns
