@@ -548,6 +548,105 @@ def run_precision(args):
     return out
 
 
+def run_planner(args):
+    """Planner experiments on one GPU, every problem 2^24 complex points (128 MiB in
+    and out, larger than L2), forward, timed with CUDA events:
+      estimate_penalty -- each size planned in estimate mode (no timing) and in
+        measure mode (candidates timed on the device), both executed: the paper's
+        estimate-mode penalty (sec. 4.3) on this hardware;
+      sizes_3600_3840_4096 -- the paper's observation (sec. 7) that lengths 3600
+        and 3840 ran faster than 4096 on its CPU, at equal points per problem;
+      prime_plans -- prime lengths with Rader (convolution length p - 1 or a
+        padded power of two) against Bluestein (smallest 2^a3^b5^c7^d or power
+        of two), each forced through a wisdom entry (sec. 4.2.5)."""
+    import torch
+
+    from paper_2602_23525_gb300 import gbfft
+    total = 1 << 24
+    x = torch.from_numpy(fft_inputs.uniform_c64(total, fft_inputs.seed_for(7))).cuda()
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    reps = max(5, args.steps)
+
+    def timed(n, flags, wisdom=None):
+        gbfft.fft_forget_wisdom()
+        if wisdom:
+            gbfft.fft_import_wisdom(wisdom)
+        b = total // n
+        t0 = time.time()
+        p = gbfft.Plan([(n, 1, 1)], [(b, n, n)], -1, flags)
+        plan_s = time.time() - t0
+        for _ in range(3):
+            gbfft.fft_execute(p.handle, x.data_ptr(), y.data_ptr(), s)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gbfft.fft_execute(p.handle, x.data_ptr(), y.data_ptr(), s)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        top = [ln.strip() for ln in p.info.splitlines()[1:] if ln.strip()]
+        kind = top[0].split(" (")[0] if top else ""
+        r = {"ms": round(ms, 4), "ns_per_point": round(ms * 1e6 / (n * b), 4),
+             "gflops": round(flops_of(n, b) / (ms * 1e-3) / 1e9, 1),
+             "gbs_algorithmic": round(16.0 * n * b / (ms * 1e-3) / 1e9, 1),
+             "launches": p.launches, "plan_s": round(plan_s, 3), "plan": kind}
+        p.destroy()
+        return r
+
+    sizes = [1 << e for e in range(4, 25)] + [1000, 2187, 3125, 3600, 3840, 7168, 10007, 12289]
+    pen = []
+    for n in sizes:
+        est = timed(n, gbfft.FFT_ESTIMATE)
+        mea = timed(n, gbfft.FFT_MEASURE)
+        pen.append({"n": n, "batch": total // n, "estimate": est, "measure": mea,
+                    "estimate_over_measure": round(est["ms"] / mea["ms"], 3)})
+    e2 = {str(n): timed(n, gbfft.FFT_MEASURE) for n in (3600, 3840, 4096)}
+    primes = []
+    for pr in (1153, 7681, 12289, 65537, 10007, 40009):
+        b = total // pr
+        key = f"r1 n={pr} is=1 os=1 v=[({b},{pr},{pr})] ip=0\t"
+        m2 = 1
+        while m2 < 2 * pr - 1:
+            m2 <<= 1
+        r2 = 1
+        while r2 < 2 * pr - 3:
+            r2 <<= 1
+        ms_ = 2 * pr - 1
+        while not _smooth7(ms_):
+            ms_ += 1
+        opts = {}
+        if _smooth13(pr - 1):
+            opts[f"rader:{pr - 1}"] = None
+        opts[f"rader:{r2}"] = None
+        opts[f"blue:{ms_}"] = None
+        opts[f"blue:{m2}"] = None
+        row = {"p": pr, "batch": b}
+        for o in opts:
+            row[o] = timed(pr, gbfft.FFT_ESTIMATE, "gbfft-wisdom 1\n" + key + o + "\n")
+        row["measured_choice"] = timed(pr, gbfft.FFT_MEASURE)
+        primes.append(row)
+    gbfft.fft_forget_wisdom()
+    return {"metric": METRIC, "unit": "GFLOP/s", "workload": "planner experiments, 2^24 points per problem, "
+            "forward", "reps": reps, "estimate_penalty": pen, "sizes_3600_3840_4096": e2, "prime_plans": primes}
+
+
+def _smooth7(m):
+    for q in (2, 3, 5, 7):
+        while m % q == 0:
+            m //= q
+    return m == 1
+
+
+def _smooth13(m):
+    for q in (2, 3, 5, 7, 11, 13):
+        while m % q == 0:
+            m //= q
+    return m == 1
+
+
 def run_serving(args):
     """The serving workload: requests of mixed shapes (rank 1-3), batches and signs
     with Poisson arrivals, admitted by a 40 GB work-buffer budget.  The arrival
@@ -595,7 +694,7 @@ def run_serving(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "uneven", "serving", "precision"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "uneven", "serving", "precision", "planner"],
                     help="sweep: the benchmark step; uneven / serving: extra workloads (their own line)")
     ap.add_argument("--requests", type=int, default=100000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: 0.7 x capacity)")
@@ -614,9 +713,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     args.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload in ("uneven", "serving", "precision"):
+    if args.workload in ("uneven", "serving", "precision", "planner"):
         if rank == 0:
-            fn = {"uneven": run_uneven, "serving": run_serving, "precision": run_precision}[args.workload]
+            fn = {"uneven": run_uneven, "serving": run_serving, "precision": run_precision,
+                  "planner": run_planner}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":

@@ -170,6 +170,8 @@ extern "C" int fft_import_wisdom(const char* text) {
       if (atoll(val.c_str() + 6) < 2) return set_err(FFT_ERR_WISDOM);
     } else if (val.rfind("blue:", 0) == 0) {
       if (atoll(val.c_str() + 5) < 3) return set_err(FFT_ERR_WISDOM);
+    } else if (val.rfind("l2fs:", 0) == 0) {
+      if (atoll(val.c_str() + 5) < 2) return set_err(FFT_ERR_WISDOM);
     } else if (val.rfind("rader:", 0) == 0) {
       if (atoll(val.c_str() + 6) < 2) return set_err(FFT_ERR_WISDOM);
     } else if (val.rfind("cluster:", 0) == 0) {

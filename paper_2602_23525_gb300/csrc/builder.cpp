@@ -1072,6 +1072,100 @@ struct Builder {
     line(depth + 1, "pointwise Y = w conj(D)");
   }
 
+  // per-stage tables [k][4] of the power-of-two pass kernels for n = 2^logn
+  const float2* p2_stage_tables(int logn) {
+    float2* tw = (float2*)dalloc(sizeof(float2) * (size_t)std::max(16, gb_p2_twiddle_elems(logn)));
+    for (int st = 1; tw && !err; ++st) {
+      int L, R, off;
+      if (!gb_p2_stage(logn, st, &L, &R, &off)) break;
+      if (gb_make_stage_twiddles(tw + off, (int64_t)1 << logn, L, R, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+    }
+    return tw;
+  }
+
+  // The four-step of eq. (2) as one persistent kernel whose intermediate stays
+  // in an L2-resident ring (l2fourstep.cu): contiguous power-of-two transforms
+  // of 2^14 .. 2^22 points, at most one vector loop.  The lag D between the A
+  // and B items of a transform is two waves of the persistent grid; the ring
+  // holds S = 2D transforms within kL2RingBytes (S > D is required).
+  static constexpr int64_t kL2RingBytes = (int64_t)64 << 20;
+
+  bool l2fs_shape(const Dim& d, const std::vector<Dim>& V, int64_t n1, int* l1, int* l2, int64_t* count,
+                  int64_t* vis, int64_t* vos) const {
+    const int lg = log2_exact(d.n), e1 = log2_exact(n1);
+    if (prec || lg < 14 || lg > 22 || e1 < 0 || d.is != 1 || d.os != 1 || V.size() > 1) return false;
+    if (!gb_l2fs_supported(e1, lg - e1)) return false;
+    *l1 = e1;
+    *l2 = lg - e1;
+    *count = V.empty() ? 1 : V[0].n;
+    *vis = V.empty() ? d.n : V[0].is;
+    *vos = V.empty() ? d.n : V[0].os;
+    return *vis > 0 && *vos > 0;
+  }
+
+  bool l2fs_ring(int l1, int l2, int64_t count, int64_t* S, int64_t* D) const {
+    int T1 = 0, T2 = 0;
+    if (!gb_l2fs_tiles(l1, l2, &T1, &T2)) return false;
+    const int64_t n = (int64_t)1 << (l1 + l2);
+    const int64_t per_t = ((int64_t)1 << l2) / T1 + ((int64_t)1 << l1) / T2;  // items per transform
+    int64_t grid = device ? gb_l2fs_grid(l1, l2) : 0;
+    if (grid <= 0) grid = (T1 << l1) <= 4096 ? 304 : 152;
+    int64_t d = std::max<int64_t>(1, (2 * grid + per_t - 1) / per_t);
+    int64_t s = 2 * d;
+    const int64_t cap = std::max<int64_t>(1, kL2RingBytes / (n * 8));
+    if (s > cap) s = cap;
+    if (d >= s) d = s - 1;
+    if (d < 1) return false;
+    if (d > count) d = count;
+    if (s > count) s = count;
+    *S = s;
+    *D = d;
+    return true;
+  }
+
+  void emit_l2fs(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t n1, int depth) {
+    int l1, l2;
+    int64_t count, vis, vos, S, D;
+    if (!l2fs_shape(d, V, n1, &l1, &l2, &count, &vis, &vos) || !l2fs_ring(l1, l2, count, &S, &D)) {
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    const int64_t n = d.n, n2 = n / n1;
+    GbL2FS k{};
+    k.logn1 = l1;
+    k.logn2 = l2;
+    k.count = count;
+    k.vis = vis;
+    k.vos = vos;
+    k.S = S;
+    k.D = D;
+    k.conj = conj;
+    k.tw1 = p2_stage_tables(l1);
+    k.tw2 = p2_stage_tables(l2);
+    const int64_t L = gb_p2_last_L(l1);
+    float2* A = (float2*)dalloc(sizeof(float2) * (size_t)(n2 * L));
+    float2* B = (float2*)dalloc(sizeof(float2) * (size_t)(n2 * 4));
+    if (A && B && gb_make_posttw(A, B, n, n2, L, 0) != cudaSuccess) err = FFT_ERR_CUDA;
+    k.ptwA = A;
+    k.ptwB = B;
+    k.status = P->d_status;
+    const size_t ring = (size_t)S * n * sizeof(float2);
+    Step s;
+    s.kind = STEP_L2FS;
+    s.l2 = k;
+    s.src = src;
+    s.dst = dst;
+    s.aux = new_scratch(ring + sizeof(unsigned) * gb_l2fs_sync_words(count));
+    P->steps.push_back(s);
+    int T1 = 0, T2 = 0;
+    gb_l2fs_tiles(l1, l2, &T1, &T2);
+    std::ostringstream o;
+    o << "pass l2-fourstep n=" << n << " = " << n1 << " x " << n2 << " (eq. 2 in one persistent kernel, "
+      << "intermediate in an L2-resident ring of " << S << " transforms, lag " << D << ") T1=" << T1 << " T2=" << T2
+      << " count=" << count << " vis=" << vis << " vos=" << vos << (conj ? " conj" : "");
+    line(depth, o.str());
+  }
+
   // Rader's algorithm (sec. 4.2.5) for a prime length p: the nonzero indices
   // permuted by powers of a generator g turn the DFT into a cyclic
   // convolution of length p - 1, evaluated by two forward FFTs of length L
@@ -1266,6 +1360,14 @@ struct Builder {
       const int64_t a = estimate_split(n);
       if (a > 1) c.push_back("split:" + std::to_string(a));
     }
+    {
+      // the four-step with its intermediate in L2 (one HBM round trip)
+      int l1, l2;
+      int64_t cnt, vi, vo, S, D;
+      const int64_t n1 = lg >= 0 ? ((int64_t)1 << (lg / 2)) : 0;
+      if (lg >= 14 && measure && l2fs_shape(d, V, n1, &l1, &l2, &cnt, &vi, &vo) && l2fs_ring(l1, l2, cnt, &S, &D))
+        c.push_back("l2fs:" + std::to_string(n1));
+    }
     MRChoice mc;
     if (!prec && mr_choose(d, V, false, &mc)) c.push_back("mr");
     if (smooth_codelet(n)) {
@@ -1449,6 +1551,8 @@ struct Builder {
         return;
       }
       emit_fourstep(d, V, src, dst, conj, n1, depth);
+    } else if (choice.rfind("l2fs:", 0) == 0) {
+      emit_l2fs(d, V, src, dst, conj, atoll(choice.c_str() + 5), depth);
     } else if (choice.rfind("rader:", 0) == 0) {
       emit_rader(d, V, src, dst, conj, atoll(choice.c_str() + 6), depth);
     } else if (choice.rfind("blue:", 0) == 0) {
@@ -1580,6 +1684,15 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
     }
     case STEP_BLUE_MUL: {
       e = gb_launch_blue_mul(s.blue, bufs[s.dst], st);
+      break;
+    }
+    case STEP_L2FS: {
+      GbL2FS k = s.l2;
+      k.in = bufs[s.src];
+      k.out = bufs[s.dst];
+      k.ring = bufs[s.aux];
+      k.sync = reinterpret_cast<unsigned*>(k.ring + k.S * ((int64_t)1 << (k.logn1 + k.logn2)));
+      e = gb_launch_l2fs(k, st);
       break;
     }
     case STEP_RADER_PRE: {

@@ -66,6 +66,35 @@ int gb_tc_supported(int logn, int load, int store, int posttw);
 int gb_tc_tile(int logn, int load, int store);
 cudaError_t gb_launch_tc(const GbP2& k, cudaStream_t st);
 
+// The four-step of eq. (2) with its intermediate kept in L2 (l2fourstep.cu):
+// contiguous transforms of n = 2^logn1 x 2^logn2 points in a batch (count,
+// vis, vos), one persistent kernel whose A items compute the n1-point column
+// DFTs (+ w_n^{l2 k1}) into a ring of S transform slots and whose B items
+// compute the n2-point row DFTs from the ring into the output (lag D < S).
+struct GbL2FS {
+  int logn1, logn2;        // column DFT length (pass A), row DFT length (pass B)
+  const float2* in;        // set at execute time
+  float2* out;
+  float2* ring;            // S * n elements (scratch)
+  unsigned* sync;          // [0] item counter, [1 + t] A items done, [1 + count + t] B items done
+  int64_t count, vis, vos;
+  int64_t S, D;
+  int conj;
+  const float2* tw1;       // stage tables of n1 and n2 (gb_make_stage_twiddles)
+  const float2* tw2;
+  const float2* ptwA;      // w_n^{l2 k1}: gb_make_posttw(ncols = n2, L = last L of n1)
+  const float2* ptwB;
+  int* status;
+  int64_t grid;            // <= 0: one CTA per SM times occupancy
+};
+// supported (logn1, logn2) and the tile shape: transforms' columns / rows per item
+int gb_l2fs_supported(int logn1, int logn2);
+int gb_l2fs_tiles(int logn1, int logn2, int* T1, int* T2);
+// persistent CTAs the launch uses on the current device (for the lag D)
+int gb_l2fs_grid(int logn1, int logn2);
+size_t gb_l2fs_sync_words(int64_t count);  // unsigned words of k.sync
+cudaError_t gb_launch_l2fs(const GbL2FS& k, cudaStream_t st);
+
 // Single-pass transforms of n = 2^13 .. 2^17 spread over a thread-block
 // cluster (cluster.cu): n = n1 x n2 (eq. (2)); CTA s of the cluster computes
 // the n1-point DFTs of columns [s n2/C, (s+1) n2/C) with the twiddles

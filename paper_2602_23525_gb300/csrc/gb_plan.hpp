@@ -47,7 +47,8 @@ enum StepKind {
   STEP_STALL = 8,  // FFT_DEBUG_STALL: a bounded wait that runs out
   STEP_RADER_PRE = 9,
   STEP_RADER_MUL = 10,
-  STEP_RADER_POST = 11
+  STEP_RADER_POST = 11,
+  STEP_L2FS = 12   // four-step with the intermediate in an L2-resident ring
 };
 
 // Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.
@@ -64,6 +65,7 @@ struct Step {
   GbCopy copy{};
   GbBlueIO blue{};
   GbRaderIO rader{};
+  GbL2FS l2{};                    // STEP_L2FS: ring and counters come from scratch buffer `aux`
   int src = BUF_IN, dst = BUF_OUT;
   int aux = -1;                   // a further buffer id (Rader's per-transform side values)
   int threads = 0;

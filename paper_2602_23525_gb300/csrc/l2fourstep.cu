@@ -1,0 +1,378 @@
+// l2fourstep.cu -- the radix-sqrt(n) step of eq. (2) for batches of
+// contiguous power-of-two transforms, n = n1 n2 = 2^14 .. 2^22, with its
+// intermediate kept in L2 (one HBM round trip per transform).
+//
+// The two passes of the four-step plan (sec. 3.3; eq. (2) with the twiddles
+// w_n^{l2 k1} fused) become two kinds of work item of one persistent kernel:
+//   A(t, j): columns l2 in [j T1, (j+1) T1) of transform t -- a tensor-map
+//            box from HBM, the n1-point DFTs over l1, the twiddle, stored as
+//            rows k1 of the transform's slot of a scratch ring (k1 n2 + l2);
+//   B(t, j): rows k1 in [j T2, (j+1) T2) of that slot -- read back from L2,
+//            the n2-point DFTs over l2, stored to Y[k1 + k2 n1] in HBM.
+// The ring holds S transforms (slot t mod S), a few tens of MiB, so the
+// intermediate stays in the 129 MB L2 instead of making a round trip
+// through HBM; only the input reads and output writes reach DRAM.
+//
+// Order and dependencies.  CTAs take items one at a time from a device
+// counter, in a fixed order: step k holds the A items of transform k and the
+// B items of transform k - D (lag D), so a B item is taken about D steps
+// after the A items it needs.  B(t, .) waits until all A items of t are done;
+// A(t, .) waits, before writing its slot, until all B items of t - S are done
+// (S > D).  An item only ever waits on items taken before it, by CTAs that
+// are running, so the kernel cannot deadlock, with or without other kernels
+// on the GPU.  Every wait is bounded by %globaltimer (2 s); a CTA whose wait
+// gives up waits (bounded) for its copies in flight, records
+// FFT_ERR_DEVICE_TIMEOUT and exits, and the CTAs that depend on it time out
+// in turn.  Completion counters and the item counter are cleared by the host
+// (cudaMemsetAsync) before each launch.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include <cstring>
+
+#include "gb_kernels.h"
+#include "gb_p2_stages.cuh"
+#include "gb_tma.cuh"
+
+namespace {
+
+struct ItemRef {
+  int kind;     // 0 A, 1 B, -1 none
+  int64_t t;    // transform
+  int64_t j;    // tile within the transform
+};
+
+// item i of the fixed order (steps of D-lagged A and B items)
+__device__ __forceinline__ ItemRef decode(int64_t i, int64_t count, int64_t D, int64_t nA, int64_t nB) {
+  ItemRef r{-1, 0, 0};
+  const int64_t head = D * nA, mid = (count - D) * (nA + nB), tail = D * nB;
+  if (i < 0) return r;
+  if (i < head) {
+    r.kind = 0;
+    r.t = i / nA;
+    r.j = i - r.t * nA;
+    return r;
+  }
+  i -= head;
+  if (i < mid) {
+    const int64_t k = D + i / (nA + nB), q = i - (i / (nA + nB)) * (nA + nB);
+    if (q < nA) {
+      r.kind = 0;
+      r.t = k;
+      r.j = q;
+    } else {
+      r.kind = 1;
+      r.t = k - D;
+      r.j = q - nA;
+    }
+    return r;
+  }
+  i -= mid;
+  if (i < tail) {
+    r.kind = 1;
+    r.t = count - D + i / nB;
+    r.j = i - (i / nB) * nB;
+  }
+  return r;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// bounded wait until *p >= target
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target) {
+  if (ld_acquire(p) >= target) return true;
+  const unsigned long long t0 = globaltimer();
+  while (ld_acquire(p) < target) {
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
+}  // namespace
+
+namespace {
+
+// cp.async of 16 bytes from global (through L2 only) into shared memory
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// TP points per item (T1 = TP / n1 columns, T2 = TP / n2 rows), 16 values a
+// thread.  Each item lands in one of two buffers, prefetched one item ahead:
+// an A item's columns by tensor-map boxes (TMA), a B item's rows of the ring
+// by cp.async through L2 (only if the A items it needs are already done;
+// else when it is processed).  Item indices are fetched two ahead, so the
+// counter's round trip is hidden.
+template <int L1, int L2, int TP, int MINB>
+__global__ void __launch_bounds__(TP / 16, MINB)
+    gb_l2fs_kernel(const __grid_constant__ GbL2FS k, const __grid_constant__ CUtensorMap tm, int tmap_ok, int pos) {
+  using CA = P2<L1>;
+  using CB = P2<L2>;
+  constexpr int N1 = CA::N, N2 = CB::N, T1 = TP / N1, T2 = TP / N2, NT = TP / 16;
+  constexpr int64_t N = (int64_t)N1 * N2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  long long* fetched = reinterpret_cast<long long*>(smem_raw + 64);  // 3 slots
+  int* ready = reinterpret_cast<int*>(smem_raw + 96);                // the next B item's inputs are complete
+  float2* ibuf = reinterpret_cast<float2*>(smem_raw + 128);
+  float2* xbuf = ibuf + 2 * TP;
+  const int tid = threadIdx.x;
+  const int64_t nA = N2 / T1, nB = N1 / T2;
+  const int64_t total = k.count * (nA + nB);
+  unsigned* ctr = k.sync;
+  unsigned* doneA = k.sync + 1;
+  unsigned* doneB = k.sync + 1 + k.count;
+
+  // pass A mapping: lanes across the T1 columns (tile loads and column stores)
+  const int at = tid % T1, au = tid / T1;
+  const int aj = tid / CA::TPT, auj = tid % CA::TPT;
+  // pass B mapping: lanes along a row for the loads, across the T2 rows for the stores
+  const int bj = tid / CB::TPT, buj = tid % CB::TPT;
+  const int bt = tid % T2, bu = tid / T2;
+
+  auto item = [&](long long i) { return i < total ? decode(i, k.count, k.D, nA, nB) : ItemRef{-1, 0, 0}; };
+
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fetched[0] = (long long)atomicAdd(ctr, 1u);
+    fetched[1] = (long long)atomicAdd(ctr, 1u);
+  }
+  __syncthreads();
+
+  uint32_t ph0 = 0, ph1 = 0;
+  bool fly0 = false, fly1 = false;  // a box issued into buffer 0 / 1 and not yet waited for
+  bool bad = false;
+
+  // prefetch item `it` into buffer b: A -> TMA boxes (thread 0); B -> cp.async
+  // of its T2 rows (all threads; the caller has checked the dependency).
+  // Every thread commits exactly one cp.async group per call.
+  auto prefetch = [&](int b, const ItemRef& it) {
+    float2* dst = ibuf + b * TP;
+    if (it.kind == 0 && tmap_ok) {
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t bar = smem_addr(bars + b);
+        expect_tx(bar, (uint32_t)(TP * 8));
+        constexpr int BOXR = N1 < 256 ? N1 : 256;
+#pragma unroll
+        for (int r0 = 0; r0 < N1; r0 += BOXR)
+          tensor_copy_4d(smem_addr(dst + r0 * T1), &tm, (int)(it.j * T1), map_coord(pos, 1, r0, (int)it.t, 0),
+                         map_coord(pos, 2, r0, (int)it.t, 0), map_coord(pos, 3, r0, (int)it.t, 0), bar);
+      }
+      (b ? fly1 : fly0) = true;
+    } else if (it.kind == 1) {
+      const float2* src = k.ring + (it.t % k.S) * N + it.j * T2 * N2;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = tid + q * NT;  // 16-byte chunk
+        cp_async16(dst + 2 * c, src + 2 * c);
+      }
+    }
+    cp_async_commit();
+  };
+
+  // A B item is prefetched only when the A items it reads are already done:
+  // the check never waits, because this CTA may itself hold one of them as
+  // its current item.  Otherwise its rows are loaded when it is processed,
+  // after a bounded wait.
+  auto inputs_done = [&](const ItemRef& it) -> int {
+    return it.kind != 1 || ld_acquire(doneA + it.t) >= (unsigned)nA;
+  };
+
+  ItemRef ci = item(fetched[0]);
+  if (tid == 0) ready[0] = inputs_done(ci);
+  __syncthreads();
+  bool cur_loaded = ready[0] != 0;
+  if (cur_loaded) prefetch(0, ci);
+  else cp_async_commit();
+  int buf = 0;
+  int slot3 = 1;  // fetched[slot3] holds the item after ci
+  float2 v[16];
+  while (ci.kind >= 0) {
+    long long f2 = 0;
+    if (tid == 0) {
+      f2 = (long long)atomicAdd(ctr, 1u);  // two ahead: used at the end of this item
+      ready[0] = inputs_done(item(fetched[slot3]));  // thread 0 wrote fetched[slot3] itself
+    }
+    __syncthreads();  // the other buffer was read by the previous item
+    const ItemRef ni = item(fetched[slot3]);
+    const bool next_loaded = ready[0] != 0;
+    if (next_loaded) prefetch(buf ^ 1, ni);
+    else cp_async_commit();
+    float2* slot = k.ring + (ci.t % k.S) * N;
+    const float2* tile = ibuf + buf * TP;
+    if (ci.kind == 0) {
+      // ---- A(t, j): columns [j T1, (j+1) T1) of transform t into the slot
+      bool fine = true;
+      if (tmap_ok) fine = mbar_wait(smem_addr(bars + buf), (buf ? ph1 : ph0) & 1);
+      if (tid == 0 && ci.t >= k.S) fine = fine && wait_count(doneB + (ci.t - k.S), (unsigned)nB);
+      if (__syncthreads_or(!fine)) {
+        bad = true;
+        break;
+      }
+      if (tmap_ok) {
+        if (buf) {
+          ++ph1;
+          fly1 = false;
+        } else {
+          ++ph0;
+          fly0 = false;
+        }
+        stage_in<L1, 0, true, T1>(v, tile + at, k.tw1, au, k.conj);
+      } else {
+        stage_in<L1, 0, true, N2>(v, k.in + ci.t * k.vis + ci.j * T1 + at, k.tw1, au, k.conj);
+      }
+      const int64_t col = ci.j * T1 + at;  // l2
+      stage_out_x<L1, 0>(v, xbuf + at * CA::PITCH, au);
+      __syncthreads();
+      later_stages<L1, 1, true>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, N2, k.tw1, auj, au,
+                                k.conj, true, k.ptwA, k.ptwB, col);
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(doneA + ci.t, 1u);
+    } else {
+      // ---- B(t, j): rows [j T2, (j+1) T2) of the slot into Y[k1 + k2 n1]
+      if (cur_loaded) {
+        cp_async_wait1();  // this item's rows (the group before the next item's)
+      } else {
+        const int fine = tid == 0 ? (int)wait_count(doneA + ci.t, (unsigned)nA) : 1;
+        if (__syncthreads_or(!fine)) {
+          bad = true;
+          break;
+        }
+        prefetch(buf, ci);
+        cp_async_wait0();
+      }
+      __syncthreads();
+      if (tid == 0) {
+        // every read of these rows has landed: the slot may be rewritten
+        __threadfence();
+        atomicAdd(doneB + ci.t, 1u);
+      }
+      const int64_t row0 = ci.j * T2;
+      stage_in<L2, 0, true, 1>(v, tile + bj * N2, k.tw2, buj, k.conj);
+      stage_out_x<L2, 0>(v, xbuf + bj * CB::PITCH, buj);
+      __syncthreads();
+      later_stages<L2, 1, false>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH, k.out + ci.t * k.vos + row0 + bt,
+                                 N1, k.tw2, buj, bu, k.conj, true, nullptr, nullptr, 0);
+    }
+    if (tid == 0) fetched[(slot3 + 1) % 3] = f2;
+    slot3 = (slot3 + 1) % 3;
+    ci = ni;
+    cur_loaded = next_loaded;
+    buf ^= 1;
+  }
+  cp_async_wait0();
+  if (bad) {
+    // a wait gave up: let the boxes this CTA issued land (bounded) before it exits
+    if (fly0) mbar_wait(smem_addr(bars + 0), ph0 & 1);
+    if (fly1) mbar_wait(smem_addr(bars + 1), ph1 & 1);
+    if (tid == 0) gb_set_status(k.status, kStatusTimeout);
+  }
+}
+
+template <int L1, int L2>
+struct L2FSCfg {
+  static constexpr int TP = (L1 + L2 <= 16) ? 4096 : 8192;
+  static constexpr int MINB = TP == 4096 ? 2 : 1;
+  static constexpr int T1 = TP >> L1, T2 = TP >> L2;
+  static constexpr int XB = (T1 * P2<L1>::PITCH > T2 * P2<L2>::PITCH) ? T1 * P2<L1>::PITCH : T2 * P2<L2>::PITCH;
+  static constexpr size_t smem = 128 + sizeof(float2) * ((size_t)2 * TP + (size_t)XB);
+};
+
+template <int L1, int L2>
+int grid_of() {
+  using G = L2FSCfg<L1, L2>;
+  auto fn = gb_l2fs_kernel<L1, L2, G::TP, G::MINB>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, G::TP / 16, G::smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+template <int L1, int L2>
+cudaError_t launch(const GbL2FS& k, cudaStream_t st) {
+  using G = L2FSCfg<L1, L2>;
+  const int64_t items = k.count * ((int64_t)(1 << L2) / G::T1 + (int64_t)(1 << L1) / G::T2);
+  int64_t grid = k.grid > 0 ? k.grid : grid_of<L1, L2>();
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  if (grid > items) grid = items;
+  cudaError_t e = cudaMemsetAsync(k.sync, 0, sizeof(unsigned) * gb_l2fs_sync_words(k.count), st);
+  if (e != cudaSuccess) return e;
+  // the input's tensor map: dims (n2 columns, n1 rows, count transforms)
+  GbP2 g{};
+  g.logn = L1;
+  g.load = GB_P2_LOAD_ROWS;
+  g.in = k.in;
+  g.V0 = 1 << L2;
+  g.vis0 = 1;
+  g.is = 1 << L2;
+  g.nb1 = k.count;
+  g.vis1 = k.vis;
+  g.nb2 = 1;
+  alignas(128) CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  int pos = 0;
+  const int tmap_ok = gb_p2_rows_map(g, G::T1, &tm, &pos);
+  gb_l2fs_kernel<L1, L2, G::TP, G::MINB><<<(unsigned)grid, G::TP / 16, G::smem, st>>>(k, tm, tmap_ok, pos);
+  return cudaGetLastError();
+}
+
+#define GB_L2FS_CASES(X) X(7, 7) X(7, 8) X(8, 8) X(8, 9) X(9, 9) X(9, 10) X(10, 10) X(10, 11) X(11, 11)
+
+}  // namespace
+
+int gb_l2fs_supported(int logn1, int logn2) {
+#define GB_L2FS_SUP(a, b) if (logn1 == a && logn2 == b) return 1;
+  GB_L2FS_CASES(GB_L2FS_SUP)
+#undef GB_L2FS_SUP
+  return 0;
+}
+
+int gb_l2fs_tiles(int logn1, int logn2, int* T1, int* T2) {
+#define GB_L2FS_T(a, b)                 \
+  if (logn1 == a && logn2 == b) {       \
+    *T1 = L2FSCfg<a, b>::T1;            \
+    *T2 = L2FSCfg<a, b>::T2;            \
+    return 1;                           \
+  }
+  GB_L2FS_CASES(GB_L2FS_T)
+#undef GB_L2FS_T
+  return 0;
+}
+
+int gb_l2fs_grid(int logn1, int logn2) {
+#define GB_L2FS_G(a, b) if (logn1 == a && logn2 == b) return grid_of<a, b>();
+  GB_L2FS_CASES(GB_L2FS_G)
+#undef GB_L2FS_G
+  return 0;
+}
+
+size_t gb_l2fs_sync_words(int64_t count) { return (size_t)(1 + 2 * count); }
+
+cudaError_t gb_launch_l2fs(const GbL2FS& k, cudaStream_t st) {
+#define GB_L2FS_L(a, b) if (k.logn1 == a && k.logn2 == b) return launch<a, b>(k, st);
+  GB_L2FS_CASES(GB_L2FS_L)
+#undef GB_L2FS_L
+  return cudaErrorInvalidValue;
+}
