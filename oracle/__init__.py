@@ -18,8 +18,14 @@ What it computes (Johnson & Frigo, *Implementing FFTs in Practice*):
   recursive mixed-radix decimation-in-time Cooley-Tukey of eq. (2) and
   Algorithm 1 (``algo="ct"``); ``"auto"`` takes direct for n <= 4096.
 
-Everything is computed in IEEE FP64 in plain C (``oracle.c``), threaded over
-the vector loops with pthreads.
+* ``rdft_r2c`` / ``rdft_c2r``: DFTs of real data (sec. 5 and 7): the forward
+  transform of a real input restricted to the non-redundant half of its
+  conjugate-symmetric spectrum (last index <= n/2), and the unnormalised
+  backward transform of such a half spectrum to real data.  Both are ``dft``
+  applied to the data widened or extended in a dense array, plus index work.
+
+Every transform is computed in IEEE FP64 in plain C (``oracle.c``), threaded
+over the vector loops with pthreads.
 """
 from __future__ import annotations
 
@@ -158,3 +164,116 @@ def dft_nd(x, sign=-1, algo="auto", threads=None):
     dims.reverse()
     y = dft(x.reshape(-1), dims, [], sign, algo=algo, threads=threads)
     return y.reshape(x.shape)
+
+
+# --------------------------------------------------------------------------- real data
+
+def _loop_offsets(loops, k):
+    """Offsets (flattened, row-major over `loops`) of stride component k (1 in, 2 out)."""
+    off = np.zeros(1, dtype=np.int64)
+    for d in loops:
+        off = (off[:, None] + np.arange(d[0], dtype=np.int64)[None, :] * int(d[k])).reshape(-1)
+    return off
+
+
+def _dense(shape_loops):
+    """(n, s, s) triples of a dense row-major layout of the given lengths."""
+    out, st = [], 1
+    for n in reversed(shape_loops):
+        out.append((n, st, st))
+        st *= n
+    return list(reversed(out))
+
+
+def rdft_r2c(x, dims, howmany=(), *, out_len=None, in_offset=0, out_offset=0, algo="auto", threads=None):
+    """DFT of real data (sec. 5 and sec. 7: real-input transforms), forward.
+
+    x       : real array; dims (n, is, os) and howmany as in ``dft``, with the
+              input strides counted in real elements and the output strides in
+              complex elements
+    returns : the complex128 output buffer holding Y[k] = sum_l x[l] prod_j
+              w_{n_j}^{l_j k_j} (w = exp(-2 pi i / n)) for every k whose last
+              index is at most n_last / 2 (integer division): the non-redundant
+              half of the conjugate-symmetric spectrum of a real input
+    The spectrum is the complex DFT of eq. (1) over all dimensions, computed by
+    ``dft`` on the input widened to complex; nothing else is computed here.
+    """
+    dims = [tuple(int(v) for v in d) for d in dims]
+    howmany = [tuple(int(v) for v in d) for d in howmany]
+    if not dims:
+        raise ValueError("a real-data transform has rank >= 1")
+    xr = np.asarray(x, dtype=np.float64).reshape(-1)
+    loops = howmany + dims
+    shape = [d[0] for d in loops]
+    half = dims[-1][0] // 2 + 1
+    hshape = shape[:-1] + [half]
+    hloops = loops[:-1] + [(half, dims[-1][1], dims[-1][2])]
+    if out_len is None:
+        _, hi = _span([(d[0], d[2]) for d in hloops])
+        out_len = out_offset + hi + 1
+    out = np.zeros(int(out_len), dtype=np.complex128)
+    if any(n == 0 for n in shape):
+        return out
+    dense = xr[in_offset + _loop_offsets(loops, 1)].astype(np.complex128)
+    ld = _dense(shape)
+    full = dft(dense, ld[len(howmany):], ld[:len(howmany)], -1, algo=algo, threads=threads)
+    full = full.reshape(shape)[..., :half].reshape(-1)
+    out[out_offset + _loop_offsets(hloops, 2)] = full
+    return out
+
+
+def rdft_c2r(X, dims, howmany=(), *, out_len=None, in_offset=0, out_offset=0, algo="auto", threads=None):
+    """Real-output DFT (sec. 5 and sec. 7), backward and unnormalised: the inverse
+    of ``rdft_r2c`` up to the factor prod(n).
+
+    X       : complex array holding the half spectrum, k_last <= n_last / 2 (the
+              last dimension has n_last // 2 + 1 entries); dims (n, is, os) with
+              the input strides in complex elements and the output strides in
+              real elements
+    returns : the float64 output buffer holding
+              y[l] = Re( sum_{k, k_last <= n_last/2} c(k_last) X[k] prod_j w_{n_j}^{-l_j k_j} ),
+              c = 1 for k_last = 0 and, for even n_last, k_last = n_last / 2,
+              else 2 -- for a conjugate-symmetric spectrum this is the sum over
+              all k of its full extension; the imaginary parts the extension
+              cannot carry (those of the k_last = 0 and n_last / 2 planes) drop out
+    Evaluated as the real part of ``dft`` (sign +1) of the weighted half
+    spectrum placed in a full-length array, zero beyond n_last / 2.
+    """
+    dims = [tuple(int(v) for v in d) for d in dims]
+    howmany = [tuple(int(v) for v in d) for d in howmany]
+    if not dims:
+        raise ValueError("a real-data transform has rank >= 1")
+    Xc = np.asarray(X, dtype=np.complex128).reshape(-1)
+    loops = howmany + dims
+    shape = [d[0] for d in loops]
+    nl = dims[-1][0]
+    half = nl // 2 + 1
+    hloops = loops[:-1] + [(half, dims[-1][1], dims[-1][2])]
+    if out_len is None:
+        _, hi = _span([(d[0], d[2]) for d in loops])
+        out_len = out_offset + hi + 1
+    out = np.zeros(int(out_len), dtype=np.float64)
+    if any(n == 0 for n in shape):
+        return out
+    hx = Xc[in_offset + _loop_offsets(hloops, 1)].reshape(shape[:-1] + [half])
+    c = np.full(half, 2.0)
+    c[0] = 1.0
+    if nl % 2 == 0:
+        c[-1] = 1.0
+    full = np.zeros(shape, dtype=np.complex128)
+    full[..., :half] = hx * c
+    ld = _dense(shape)
+    y = dft(full.reshape(-1), ld[len(howmany):], ld[:len(howmany)], 1, algo=algo, threads=threads)
+    out[out_offset + _loop_offsets(loops, 2)] = y.real
+    return out
+
+
+def _span(pairs):
+    lo = hi = 0
+    for n, s in pairs:
+        e = (n - 1) * s
+        if e < 0:
+            lo += e
+        else:
+            hi += e
+    return lo, hi
