@@ -103,6 +103,39 @@ fft_plan fft_plan_dft(int rank, const fft_iodim *dims, int howmany_rank,
                       const fft_iodim *howmany_dims, int sign, unsigned flags);
 
 /*
+ * fft_plan_dft_r2c / fft_plan_dft_c2r -- DFTs of real data (sec. 5: the
+ * real-input specialisation saves about a factor of two; sec. 7: real-data
+ * transforms as part of the library's generality).  The problem is
+ * dft(N, V, I, O) of a real array:
+ *   r2c: real input x (FP32), complex64 output Y[k] = sum_l x[l] w^{l k}
+ *        (sign -1, eq. (1) over every dimension) for the indices whose last
+ *        component k_last <= n_last / 2 (integer division): the
+ *        non-redundant half of the conjugate-symmetric spectrum, so the last
+ *        output dimension has n_last / 2 + 1 entries;
+ *   c2r: complex64 input holding such a half spectrum, real output
+ *        y[l] = Re( sum_{k_last <= n_last/2} c(k_last) X[k] w^{-l k} ), c = 1
+ *        for k_last = 0 and (n_last even) k_last = n_last / 2, else 2 -- the
+ *        unnormalised backward transform of the conjugate-symmetric extension
+ *        (c2r(r2c(x)) = prod(n) x); the imaginary parts of the
+ *        self-conjugate planes k_last = 0, n_last / 2 drop out.
+ * dims[i] = (n, is, os) with n the real (logical) length; strides count
+ * elements of the array they step through: FP32 values on the real side,
+ * complex64 values on the complex side (so the last complex dimension has
+ * n_last / 2 + 1 entries along its stride).  howmany_dims likewise.
+ *   rank in [1, 3], howmany_rank in [0, 3]; flags: FFT_ESTIMATE,
+ *   FFT_WISDOM_ONLY, FFT_DEBUG_STALL (FFT_INPLACE, FFT_EXTERNAL_SCRATCH and
+ *   the tensor-core flags return FFT_ERR_UNSUPPORTED).
+ * Execute with fft_execute(plan, in, out, stream): in and out do not
+ * overlap; element 0 of the real array must be 8-byte aligned (even
+ * lengths with unit real stride read or write it as complex pairs).  The
+ * input is not modified.  Errors as fft_plan_dft.
+ */
+fft_plan fft_plan_dft_r2c(int rank, const fft_iodim *dims, int howmany_rank,
+                          const fft_iodim *howmany_dims, unsigned flags);
+fft_plan fft_plan_dft_c2r(int rank, const fft_iodim *dims, int howmany_rank,
+                          const fft_iodim *howmany_dims, unsigned flags);
+
+/*
  * fft_execute -- run a plan (sec. 4.2: the plan's steps, in order).
  *   in, out : device pointers to element 0 of complex64 arrays that cover
  *             every addressed element; caller-owned.  For an out-of-place
@@ -168,10 +201,13 @@ int fft_plan_explain(int rank, const fft_iodim *dims, int howmany_rank,
                      size_t len);
 
 /* Algorithmic bytes of one execution: 16 bytes per transformed point
- * (8 read + 8 written), the unit used for the HBM roofline. */
+ * (8 read + 8 written), the unit used for the HBM roofline; for real-data
+ * plans 4 bytes per real value plus 8 per complex value of the half
+ * spectrum. */
 double fft_plan_bytes(fft_plan p);
 
-/* Flops of one execution under the 5 N log2 N convention (sec. 1). */
+/* Flops of one execution under the 5 N log2 N convention (sec. 1); real-data
+ * plans count half of it, 2.5 N log2 N. */
 double fft_plan_flops(fft_plan p);
 
 /* Number of kernel launches one fft_execute enqueues. */

@@ -71,6 +71,45 @@ fft_plan fft_plan_dft(int rank, const fft_iodim* dims, int howmany_rank, const f
   return p;
 }
 
+static fft_plan plan_real(int rank, const fft_iodim* dims, int howmany_rank, const fft_iodim* howmany_dims,
+                          int kind, unsigned flags) {
+  Problem P;
+  int rc = canonicalize_real(rank, dims, howmany_rank, howmany_dims, kind, flags, P);
+  if (rc != FFT_OK) {
+    set_err(rc);
+    return nullptr;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    set_err(FFT_ERR_NO_DEVICE);
+    return nullptr;
+  }
+  fft_plan p = new (std::nothrow) fft_plan_s;
+  if (!p) {
+    set_err(FFT_ERR_OOM);
+    return nullptr;
+  }
+  rc = build_plan(P, true, &p->d);
+  if (rc != FFT_OK) {
+    delete p;
+    set_err(rc);
+    return nullptr;
+  }
+  set_err(FFT_OK);
+  return p;
+}
+
+fft_plan fft_plan_dft_r2c(int rank, const fft_iodim* dims, int howmany_rank, const fft_iodim* howmany_dims,
+                          unsigned flags) {
+  return plan_real(rank, dims, howmany_rank, howmany_dims, 1, flags);
+}
+
+fft_plan fft_plan_dft_c2r(int rank, const fft_iodim* dims, int howmany_rank, const fft_iodim* howmany_dims,
+                          unsigned flags) {
+  return plan_real(rank, dims, howmany_rank, howmany_dims, 2, flags);
+}
+
 int fft_plan_explain(int rank, const fft_iodim* dims, int howmany_rank, const fft_iodim* howmany_dims, int sign,
                      unsigned flags, char* buf, size_t len) {
   Problem P;

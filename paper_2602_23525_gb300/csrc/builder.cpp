@@ -1290,6 +1290,193 @@ struct Builder {
     line(depth + 1, "pointwise Y[0] = x0 + dc, Y[g^-q] = x0 + conj(D[q])");
   }
 
+  // ---------------------------------------------------------------- real data
+  // DFTs of real data (sec. 5, sec. 7), built from the complex plans above and
+  // the pointwise steps of real.cu.  `loops` are the vector loops of the 1-D
+  // real transform, strides in the units of each side.
+
+  // dense row-major strides (last loop fastest) of loops of the given lengths, times unit
+  static std::vector<int64_t> dense_strides(const std::vector<Dim>& loops, int64_t unit) {
+    std::vector<int64_t> st(loops.size());
+    int64_t s = unit;
+    for (int i = (int)loops.size() - 1; i >= 0; --i) {
+      st[i] = s;
+      s *= loops[i].n;
+    }
+    return st;
+  }
+
+  bool real_io(GbRealIO* r, int64_t n, int64_t is, int64_t os, const std::vector<Dim>& loops, bool in_side,
+               bool out_side, int64_t in_div = 1, int64_t out_div = 1) {
+    if ((int)loops.size() > GB_MAX_VDIMS) {
+      err = FFT_ERR_UNSUPPORTED;
+      return false;
+    }
+    memset(r, 0, sizeof(*r));
+    r->n = n;
+    r->m = n / 2;
+    r->is = is;
+    r->os = os;
+    r->nv = (int)loops.size();
+    r->count = 1;
+    for (int i = 0; i < r->nv; ++i) {
+      r->vn[i] = loops[i].n;
+      r->vis[i] = in_side ? loops[i].is / in_div : 0;
+      r->vos[i] = out_side ? loops[i].os / out_div : 0;
+      r->count *= loops[i].n;
+    }
+    if (r->nv == 0) {
+      r->nv = 1;
+      r->vn[0] = 1;
+    }
+    r->tw = roots(n);
+    return true;
+  }
+
+  void emit_r2c_1d(const Dim& d, const std::vector<Dim>& loops, int src, int dst, int depth) {
+    const int64_t n = d.n, half = n / 2 + 1;
+    bool pairs = n % 2 == 0 && d.is == 1;
+    for (const Dim& L : loops) pairs = pairs && (L.is % 2 == 0);
+    int64_t count = 1;
+    for (const Dim& L : loops) count *= L.n;
+    std::ostringstream o;
+    Step s;
+    if (pairs) {
+      const int64_t m = n / 2;
+      o << "real-input dft n=" << n << ": the input read as " << m << " complex pairs, a complex dft of " << m
+        << ", then the half spectrum (eq. 2 with n1 = 2)";
+      line(depth, o.str());
+      std::vector<Dim> Vc;
+      for (const Dim& L : loops) Vc.push_back({L.n, L.is / 2, L.os});
+      solve_rank1({m, 1, d.os}, Vc, src, dst, 0, depth + 1);
+      if (err || !real_io(&s.real, n, 0, d.os, loops, false, true)) return;
+      for (int i = 0; i < s.real.nv && !loops.empty(); ++i) s.real.vis[i] = s.real.vos[i];
+      s.kind = STEP_R2C_POST;
+      s.src = dst;
+      s.dst = dst;
+      P->steps.push_back(s);
+      line(depth + 1, "pointwise X[k] = Ze[k] + w_n^k Zo[k], X[m-k] = conj(Ze[k] - w_n^k Zo[k]), in place");
+      P->align8_in = true;
+      return;
+    }
+    o << "real-input dft n=" << n << ": widened to complex, a complex dft of " << n << ", the half spectrum kept";
+    line(depth, o.str());
+    const int S1 = new_scratch((size_t)count * n * sizeof(float2));
+    const int S2 = new_scratch((size_t)count * n * sizeof(float2));
+    if (!real_io(&s.real, n, d.is, 0, loops, true, false)) return;
+    s.kind = STEP_R2C_PROMOTE;
+    s.src = src;
+    s.dst = S1;
+    P->steps.push_back(s);
+    line(depth + 1, "pointwise promote x -> (x, 0)");
+    solve_rank1({n, 1, 1}, {{count, n, n}}, S1, S2, 0, depth + 1);
+    if (err) return;
+    const std::vector<int64_t> ds = dense_strides(loops, n);
+    std::vector<Dim> cp{{half, 1, d.os}};
+    for (size_t i = 0; i < loops.size(); ++i) cp.push_back({loops[i].n, ds[i], loops[i].os});
+    emit_copy(cp, S2, dst, depth + 1);
+  }
+
+  void emit_c2r_1d(const Dim& d, const std::vector<Dim>& loops, int src, int dst, int depth) {
+    const int64_t n = d.n;
+    bool pairs = n % 2 == 0 && d.os == 1;
+    for (const Dim& L : loops) pairs = pairs && (L.os % 2 == 0);
+    int64_t count = 1;
+    for (const Dim& L : loops) count *= L.n;
+    std::ostringstream o;
+    Step s;
+    if (pairs) {
+      const int64_t m = n / 2;
+      o << "real-output dft n=" << n << ": the half spectrum folded to " << m << " complex values, a backward "
+        << "complex dft of " << m << " written as real pairs";
+      line(depth, o.str());
+      const int S = new_scratch((size_t)count * m * sizeof(float2));
+      if (!real_io(&s.real, n, d.is, 0, loops, true, false)) return;
+      s.kind = STEP_C2R_PRE;
+      s.src = src;
+      s.dst = S;
+      P->steps.push_back(s);
+      line(depth + 1, "pointwise W[k] = (X[k] + conj X[m-k]) + i w_n^-k (X[k] - conj X[m-k])");
+      const std::vector<int64_t> ds = dense_strides(loops, m);
+      std::vector<Dim> Vc;
+      for (size_t i = 0; i < loops.size(); ++i) Vc.push_back({loops[i].n, ds[i], loops[i].os / 2});
+      solve_rank1({m, 1, 1}, Vc, S, dst, 1, depth + 1);
+      P->align8_out = true;
+      return;
+    }
+    o << "real-output dft n=" << n << ": the conjugate-symmetric extension, a backward complex dft of " << n
+      << ", the real parts kept";
+    line(depth, o.str());
+    const int S1 = new_scratch((size_t)count * n * sizeof(float2));
+    const int S2 = new_scratch((size_t)count * n * sizeof(float2));
+    if (!real_io(&s.real, n, d.is, 0, loops, true, false)) return;
+    s.kind = STEP_C2R_EXPAND;
+    s.src = src;
+    s.dst = S1;
+    P->steps.push_back(s);
+    line(depth + 1, "pointwise conjugate-symmetric extension (self-conjugate bins real)");
+    solve_rank1({n, 1, 1}, {{count, n, n}}, S1, S2, 1, depth + 1);
+    if (err) return;
+    Step r;
+    if (!real_io(&r.real, n, 0, d.os, loops, false, true)) return;
+    r.kind = STEP_C2R_REAL;
+    r.src = S2;
+    r.dst = dst;
+    P->steps.push_back(r);
+    line(depth + 1, "pointwise y = Re(w)");
+  }
+
+  // a real-data problem: the 1-D real transform along the last dimension and
+  // complex DFTs along the others (separable, sec. 4.1)
+  void solve_real(const Problem& Q, int depth) {
+    const Dim d = Q.N.back();
+    const std::vector<Dim> O(Q.N.begin(), Q.N.end() - 1);
+    const int64_t half = d.n / 2 + 1;
+    if (Q.kind == 1) {
+      std::vector<Dim> loops = O;
+      loops.insert(loops.end(), Q.V.begin(), Q.V.end());
+      emit_r2c_1d(d, loops, BUF_IN, BUF_OUT, depth);
+      std::vector<int> order(O.size());
+      for (size_t i = 0; i < O.size(); ++i) order[i] = (int)i;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return iabs64(O[a].os) < iabs64(O[b].os); });
+      for (int a : order) {
+        if (err) return;
+        std::vector<Dim> others;
+        for (size_t b = 0; b < O.size(); ++b)
+          if ((int)b != a) others.push_back({O[b].n, O[b].os, O[b].os});
+        others.push_back({half, d.os, d.os});
+        for (const Dim& v : Q.V) others.push_back({v.n, v.os, v.os});
+        solve_rank1({O[a].n, O[a].os, O[a].os}, others, BUF_OUT, BUF_OUT, 0, depth);
+      }
+      return;
+    }
+    if (O.empty()) {
+      emit_c2r_1d(d, Q.V, BUF_IN, BUF_OUT, depth);
+      return;
+    }
+    // backward complex DFTs over the other dimensions, from the input into a
+    // dense scratch [V][O][half], then the real transform from there
+    std::vector<Dim> shape = Q.V;
+    shape.insert(shape.end(), O.begin(), O.end());
+    shape.push_back({half, 0, 0});
+    const std::vector<int64_t> ds = dense_strides(shape, 1);
+    int64_t total = 1;
+    for (const Dim& x : shape) total *= x.n;
+    const int S = new_scratch((size_t)total * sizeof(float2));
+    const size_t nv = Q.V.size();
+    std::vector<Dim> Od, vec;
+    for (size_t i = 0; i < O.size(); ++i) Od.push_back({O[i].n, O[i].is, ds[nv + i]});
+    vec.push_back({half, d.is, 1});
+    for (size_t j = 0; j < nv; ++j) vec.push_back({Q.V[j].n, Q.V[j].is, ds[j]});
+    line(depth, "complex dfts over the other dimensions into a dense work array");
+    solve(Od, vec, BUF_IN, S, 1, depth + 1);
+    if (err) return;
+    std::vector<Dim> loops;
+    for (size_t i = 0; i < O.size(); ++i) loops.push_back({O[i].n, ds[nv + i], O[i].os});
+    for (size_t j = 0; j < nv; ++j) loops.push_back({Q.V[j].n, ds[j], Q.V[j].os});
+    emit_c2r_1d({d.n, 1, d.os}, loops, S, BUF_OUT, depth);
+  }
+
   // ---------------------------------------------------------------- planner
 
   std::string key_rank1(const Dim& d, const std::vector<Dim>& V, bool inplace) const {
@@ -1695,6 +1882,15 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
       e = gb_launch_l2fs(k, st);
       break;
     }
+    case STEP_R2C_POST: e = gb_launch_r2c_post(s.real, bufs[s.dst], st); break;
+    case STEP_R2C_PROMOTE:
+      e = gb_launch_r2c_promote(s.real, reinterpret_cast<const float*>(bufs[s.src]), bufs[s.dst], st);
+      break;
+    case STEP_C2R_PRE: e = gb_launch_c2r_pre(s.real, bufs[s.src], bufs[s.dst], st); break;
+    case STEP_C2R_EXPAND: e = gb_launch_c2r_expand(s.real, bufs[s.src], bufs[s.dst], st); break;
+    case STEP_C2R_REAL:
+      e = gb_launch_c2r_real(s.real, bufs[s.src], reinterpret_cast<float*>(bufs[s.dst]), st);
+      break;
     case STEP_RADER_PRE: {
       GbRaderIO r = s.rader;
       r.in = bufs[s.src];
@@ -1813,20 +2009,34 @@ int build_plan(const Problem& P, bool device, PlanData* out) {
   out->inplace = (P.flags & FFT_INPLACE) != 0;
   out->external_scratch = (P.flags & FFT_EXTERNAL_SCRATCH) != 0;
   std::ostringstream head;
-  head << "dft rank=" << P.N.size() << " n=" << dims_str(P.N) << " howmany=" << dims_str(P.V)
+  static const char* kinds[] = {"dft", "rdft r2c", "rdft c2r"};
+  head << kinds[P.kind] << " rank=" << P.N.size() << " n=" << dims_str(P.N) << " howmany=" << dims_str(P.V)
        << " sign=" << P.sign << (out->inplace ? " in-place" : "") << ((P.flags & FFT_ESTIMATE) ? " estimate" : "")
        << "\n";
   if (P.empty) {
     out->info = head.str() + "  empty problem: no-op\n";
     return FFT_OK;
   }
-  footprint(P.N, P.V, true, &out->in_lo, &out->in_hi);
-  footprint(P.N, P.V, false, &out->out_lo, &out->out_hi);
   int64_t pts = 1, count = 1;
   for (const Dim& d : P.N) pts *= d.n;
   for (const Dim& d : P.V) count *= d.n;
-  out->bytes = 16.0 * (double)pts * (double)count;
-  out->flops = pts > 1 ? 5.0 * (double)pts * std::log2((double)pts) * (double)count : 0.0;
+  if (P.kind == 0) {
+    footprint(P.N, P.V, true, &out->in_lo, &out->in_hi);
+    footprint(P.N, P.V, false, &out->out_lo, &out->out_hi);
+    out->bytes = 16.0 * (double)pts * (double)count;
+    out->flops = pts > 1 ? 5.0 * (double)pts * std::log2((double)pts) * (double)count : 0.0;
+  } else {
+    // the complex side's last dimension has n / 2 + 1 entries; real sides are FP32
+    std::vector<Dim> H = P.N;
+    H.back().n = H.back().n / 2 + 1;
+    const int64_t hpts = pts / P.N.back().n * H.back().n;
+    footprint(P.kind == 1 ? P.N : H, P.V, true, &out->in_lo, &out->in_hi);
+    footprint(P.kind == 1 ? H : P.N, P.V, false, &out->out_lo, &out->out_hi);
+    out->in_elem = P.kind == 1 ? 4 : 8;
+    out->out_elem = P.kind == 1 ? 8 : 4;
+    out->bytes = (4.0 * (double)pts + 8.0 * (double)hpts) * (double)count;
+    out->flops = pts > 1 ? 2.5 * (double)pts * std::log2((double)pts) * (double)count : 0.0;
+  }
   if (device) {
     if (cudaGetDevice(&out->device) != cudaSuccess) {
       cudaGetLastError();
@@ -1868,7 +2078,8 @@ int build_plan(const Problem& P, bool device, PlanData* out) {
     b.line(1, "debug stall: one wait on an mbarrier nothing arrives on, bounded at 50 ms (reports "
               "FFT_ERR_DEVICE_TIMEOUT)");
   }
-  b.solve(P.N, P.V, BUF_IN, out->inplace ? BUF_IN : BUF_OUT, conj, 1);
+  if (P.kind) b.solve_real(P, 1);
+  else b.solve(P.N, P.V, BUF_IN, out->inplace ? BUF_IN : BUF_OUT, conj, 1);
   if (!b.err && device && cudaStreamSynchronize(0) != cudaSuccess) b.err = FFT_ERR_CUDA;
   out->info = head.str() + b.info.str();
   if (b.err) {
@@ -1884,12 +2095,13 @@ int check_execute_args(const PlanData* p, const void* in, const void* out) {
   if (p->inplace) {
     if (in != out) return FFT_ERR_INPLACE_MISMATCH;
   } else {
-    const char* a0 = (const char*)in + 8 * p->in_lo;
-    const char* a1 = (const char*)in + 8 * (p->in_hi + 1);
-    const char* b0 = (const char*)out + 8 * p->out_lo;
-    const char* b1 = (const char*)out + 8 * (p->out_hi + 1);
+    const char* a0 = (const char*)in + p->in_elem * p->in_lo;
+    const char* a1 = (const char*)in + p->in_elem * (p->in_hi + 1);
+    const char* b0 = (const char*)out + p->out_elem * p->out_lo;
+    const char* b1 = (const char*)out + p->out_elem * (p->out_hi + 1);
     if (a0 < b1 && b0 < a1) return FFT_ERR_ALIAS;
   }
+  if ((p->align8_in && ((uintptr_t)in & 7)) || (p->align8_out && ((uintptr_t)out & 7))) return FFT_ERR_INVALID_ARG;
   return FFT_OK;
 }
 

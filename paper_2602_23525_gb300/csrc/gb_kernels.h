@@ -191,6 +191,31 @@ cudaError_t gb_launch_rader_pre(const GbRaderIO& b, float2* work, float2* side, 
 cudaError_t gb_launch_rader_mul(const GbRaderIO& b, float2* data, float2* side, cudaStream_t st);
 cudaError_t gb_launch_rader_post(const GbRaderIO& b, const float2* data, const float2* side, cudaStream_t st);
 
+// Real-data steps (real.cu).  One transform of real length n per vector
+// index; strides along the transform and of the vector loops in the units of
+// the array each step reads or writes (FP32 values on a real side, complex64
+// values on a complex side).
+struct GbRealIO {
+  int64_t n, m;        // real length, m = n / 2
+  int64_t is, os;      // strides along the transform (input side, output side)
+  int nv;
+  int64_t vn[GB_MAX_VDIMS], vis[GB_MAX_VDIMS], vos[GB_MAX_VDIMS];
+  int64_t count;       // product of vn
+  const float2* tw;    // w_n^k = exp(-2 pi i k / n), k < n
+};
+// in place on the complex array z (element 0 of transform v at the vector
+// offset, stride os): Z[k], k < m, the DFT of the real input read as m pairs
+// -> X[k], k <= m (writes entry m)
+cudaError_t gb_launch_r2c_post(const GbRealIO& r, float2* z, cudaStream_t st);
+// real x (strides is, vis) -> dense complex w[v n + l] = (x, 0)
+cudaError_t gb_launch_r2c_promote(const GbRealIO& r, const float* x, float2* w, cudaStream_t st);
+// half spectrum X (strides is, vis) -> dense w[v m + k] = (X[k] + conj X[m-k]) + i w_n^{-k} (X[k] - conj X[m-k])
+cudaError_t gb_launch_c2r_pre(const GbRealIO& r, const float2* X, float2* w, cudaStream_t st);
+// half spectrum X -> dense w[v n + k], the conjugate-symmetric extension
+cudaError_t gb_launch_c2r_expand(const GbRealIO& r, const float2* X, float2* w, cudaStream_t st);
+// dense complex w[v n + l] -> real y (strides os, vos): y = Re w
+cudaError_t gb_launch_c2r_real(const GbRealIO& r, const float2* w, float* y, cudaStream_t st);
+
 // Persistent executor of several plans in one launch (stockham.cu).  Work
 // items are (segment, tile); a segment is one step of one plan and may wait
 // for the segment holding the previous step of the same plan.

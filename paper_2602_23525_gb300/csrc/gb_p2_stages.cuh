@@ -41,6 +41,14 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 
 __device__ __forceinline__ int phys(int i) { return i + (i >> 5); }
 
+// barrier of the threads that compute: the whole CTA (NBT = 0), or the first
+// NBT threads on named barrier 1 (kernels with a separate control warp)
+template <int NBT>
+__device__ __forceinline__ void gb_bar() {
+  if constexpr (NBT == 0) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory");
+}
+
 template <int R>
 __device__ __forceinline__ void codelet(float2* v);
 template <> __device__ __forceinline__ void codelet<2>(float2* v) { gb_dft2(v); }
@@ -163,7 +171,7 @@ __device__ __forceinline__ void stage_out_g(const float2* v, float2* dst, int64_
   }
 }
 
-template <int LOGN, int S, bool POSTTW, bool PW = false>
+template <int LOGN, int S, bool POSTTW, bool PW = false, int NBT = 0>
 __device__ __forceinline__ void later_stages(float2* v, float2* xrow_j, float2* xrow_s, float2* gout,
                                              int64_t ostride, const float2* __restrict__ twt, int uj, int us,
                                              int conj, bool valid, const float2* A, const float2* Bt, int64_t col,
@@ -176,11 +184,11 @@ __device__ __forceinline__ void later_stages(float2* v, float2* xrow_j, float2* 
       if (valid) stage_out_g<LOGN, POSTTW, PW>(v, gout, ostride, us, conj, A, Bt, col, e, t);
     } else {
       stage_in<LOGN, S, false, 1>(v, xrow_j, twt, uj, conj);
-      __syncthreads();
+      gb_bar<NBT>();
       stage_out_x<LOGN, S>(v, xrow_j, uj);
-      __syncthreads();
-      later_stages<LOGN, S + 1, POSTTW, PW>(v, xrow_j, xrow_s, gout, ostride, twt, uj, us, conj, valid, A, Bt, col,
-                                            e, t);
+      gb_bar<NBT>();
+      later_stages<LOGN, S + 1, POSTTW, PW, NBT>(v, xrow_j, xrow_s, gout, ostride, twt, uj, us, conj, valid, A, Bt,
+                                                 col, e, t);
     }
   }
 }

@@ -22,6 +22,7 @@ struct Dim {
 // A canonical problem dft(N, V, I, O) without its pointers.
 struct Problem {
   std::vector<Dim> N, V;
+  int kind = 0;  // 0 complex, 1 real input (r2c), 2 real output (c2r)
   int sign = -1;
   unsigned flags = 0;
   bool empty = false;
@@ -48,7 +49,12 @@ enum StepKind {
   STEP_RADER_PRE = 9,
   STEP_RADER_MUL = 10,
   STEP_RADER_POST = 11,
-  STEP_L2FS = 12   // four-step with the intermediate in an L2-resident ring
+  STEP_L2FS = 12,  // four-step with the intermediate in an L2-resident ring
+  STEP_R2C_POST = 13,    // real input: half spectrum from the half-length complex DFT, in place
+  STEP_R2C_PROMOTE = 14, // real input widened to complex
+  STEP_C2R_PRE = 15,     // real output: the half-length complex input of the backward DFT
+  STEP_C2R_EXPAND = 16,  // half spectrum extended to the full conjugate-symmetric spectrum
+  STEP_C2R_REAL = 17     // real parts to the real output
 };
 
 // Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.
@@ -66,6 +72,7 @@ struct Step {
   GbBlueIO blue{};
   GbRaderIO rader{};
   GbL2FS l2{};                    // STEP_L2FS: ring and counters come from scratch buffer `aux`
+  GbRealIO real{};                // real-data steps
   int src = BUF_IN, dst = BUF_OUT;
   int aux = -1;                   // a further buffer id (Rader's per-transform side values)
   int threads = 0;
@@ -89,7 +96,9 @@ struct PlanData {
   bool done_valid = false;
   std::string info;
   double bytes = 0.0, flops = 0.0;
-  int64_t in_lo = 0, in_hi = 0, out_lo = 0, out_hi = 0;
+  int64_t in_lo = 0, in_hi = 0, out_lo = 0, out_hi = 0;  // footprints in elements
+  int in_elem = 8, out_elem = 8;                          // element bytes (4 on a real side)
+  bool align8_in = false, align8_out = false;             // a real side read or written as complex pairs
   bool inplace = false;
   int device = -1;
 };
@@ -99,6 +108,9 @@ extern thread_local int g_last_error;
 int set_err(int e);
 int canonicalize(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, int sign, unsigned flags,
                  Problem& P);
+// a real-data problem (kind 1 r2c, 2 c2r); strides as given (real or complex units per side)
+int canonicalize_real(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, int kind, unsigned flags,
+                      Problem& P);
 void footprint(const std::vector<Dim>& N, const std::vector<Dim>& V, bool input, int64_t* lo, int64_t* hi);
 std::string dims_str(const std::vector<Dim>& v);
 bool smooth_codelet(int64_t n);

@@ -103,183 +103,216 @@ namespace {
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// the mbarrier tracks the completion of this thread's earlier cp.async copies
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+struct ItemSlot {
+  long long t, j;
+  int kind;  // 0 A, 1 B, -1 no more items, -2 abort
+};
 
 // TP points per item (T1 = TP / n1 columns, T2 = TP / n2 rows), 16 values a
-// thread.  Each item lands in one of two buffers, prefetched one item ahead:
-// an A item's columns by tensor-map boxes (TMA), a B item's rows of the ring
-// by cp.async through L2 (only if the A items it needs are already done;
-// else when it is processed).  Item indices are fetched two ahead, so the
-// counter's round trip is hidden.
+// compute thread, NT = TP / 16 compute threads plus one control warp.
+//   control warp: takes the next item from the device counter, waits
+//     (bounded) until its inputs are complete (B: the A items of its
+//     transform; A: the B items of the transform whose slot it rewrites),
+//     fills landing buffer b (A: tensor-map boxes; B: cp.async of the ring
+//     rows through L2) and arrives on full[b]; once the compute warps arrive
+//     on done[b] it publishes the finished item to the other CTAs (a
+//     gpu-scope fence, then the completion counter).  It alone stalls on
+//     global round trips.
+//   compute warps: wait on full[b], compute the item's stages (named barrier
+//     1 among themselves), store, arrive on done[b].
 template <int L1, int L2, int TP, int MINB>
-__global__ void __launch_bounds__(TP / 16, MINB)
+__global__ void __launch_bounds__(TP / 16 + 32, MINB)
     gb_l2fs_kernel(const __grid_constant__ GbL2FS k, const __grid_constant__ CUtensorMap tm, int tmap_ok, int pos) {
   using CA = P2<L1>;
   using CB = P2<L2>;
   constexpr int N1 = CA::N, N2 = CB::N, T1 = TP / N1, T2 = TP / N2, NT = TP / 16;
   constexpr int64_t N = (int64_t)N1 * N2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-  long long* fetched = reinterpret_cast<long long*>(smem_raw + 64);  // 3 slots
-  int* ready = reinterpret_cast<int*>(smem_raw + 96);                // the next B item's inputs are complete
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                  // full[2], done[2]
+  ItemSlot* info = reinterpret_cast<ItemSlot*>(smem_raw + 64);             // 2 x 24 bytes
   float2* ibuf = reinterpret_cast<float2*>(smem_raw + 128);
   float2* xbuf = ibuf + 2 * TP;
   const int tid = threadIdx.x;
   const int64_t nA = N2 / T1, nB = N1 / T2;
   const int64_t total = k.count * (nA + nB);
-  unsigned* ctr = k.sync;
-  unsigned* doneA = k.sync + 1;
-  unsigned* doneB = k.sync + 1 + k.count;
 
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      // full: one arrival per control lane (plain, with the expected bytes, or
+      // when its cp.async copies land) plus lane 0's release of info[b]
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(33));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 2 + b)), "r"(NT));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (tid >= NT) {
+    // ---------------------------------------------------------------- control warp
+    const int lane = tid - NT;
+    unsigned* ctr = k.sync;
+    unsigned* doneA = k.sync + 1;
+    unsigned* doneB = k.sync + 1 + k.count;
+    ItemSlot pend[2] = {{0, 0, -1}, {0, 0, -1}};  // item in buffer b, not yet published
+    bool armed_tma[2] = {false, false};
+    uint32_t armed_par[2] = {0, 0};
+    // publish item pend[b] (lane 0): the compute warps' stores, ordered before
+    // their arrival on done[b], reach gpu scope before the completion count
+    auto publish = [&](int b) {
+      if (lane == 0 && pend[b].kind >= 0) {
+        __threadfence();
+        atomicAdd((pend[b].kind == 0 ? doneA : doneB) + pend[b].t, 1u);
+      }
+      pend[b].kind = -1;
+    };
+    // bounded wait (lane 0) until *c >= target.  The item this CTA computes
+    // in the other buffer may be one of those waited for: it is published as
+    // soon as the compute warps are done with it, inside the wait.
+    auto wait_dep = [&](const unsigned* c, unsigned target, int other, uint32_t other_par) -> bool {
+      const unsigned long long t0 = globaltimer();
+      while (ld_acquire(c) < target) {
+        if (pend[other].kind >= 0 && mbar_try(smem_addr(bars + 2 + other), other_par)) publish(other);
+        if (globaltimer() - t0 > kWaitLimitNs) return false;
+        __nanosleep(64);
+      }
+      return true;
+    };
+    bool fail = false;
+    int it = 0;
+    for (;; ++it) {
+      const int b = it & 1;
+      const uint32_t full = smem_addr(bars + b), done = smem_addr(bars + 2 + b);
+      if (it >= 2) {
+        if (!mbar_wait(done, ((it - 2) >> 1) & 1)) {
+          fail = true;
+          break;
+        }
+        armed_tma[b] = false;
+        publish(b);  // unless published already during a dependency wait
+      }
+      long long idx = 0;
+      if (lane == 0) idx = (long long)atomicAdd(ctr, 1u);
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      ItemSlot r{0, 0, -1};
+      if (idx < total) {
+        const ItemRef d = decode(idx, k.count, k.D, nA, nB);
+        r = ItemSlot{d.t, d.j, d.kind};
+      }
+      int ok = 1;
+      if (lane == 0) {
+        const int o = b ^ 1;
+        const uint32_t op = ((it - 1) >> 1) & 1;  // phase of the other buffer's item (it - 1)
+        if (r.kind == 1) ok = wait_dep(doneA + r.t, (unsigned)nA, o, op);
+        else if (r.kind == 0 && r.t >= k.S) ok = wait_dep(doneB + (r.t - k.S), (unsigned)nB, o, op);
+        info[b] = r;
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        fail = true;
+        break;
+      }
+      __syncwarp();
+      float2* dst = ibuf + b * TP;
+      if (r.kind == 0 && tmap_ok) {
+        if (lane == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          expect_tx(full, (uint32_t)(TP * 8));
+          constexpr int BOXR = N1 < 256 ? N1 : 256;
+#pragma unroll
+          for (int r0 = 0; r0 < N1; r0 += BOXR)
+            tensor_copy_4d(smem_addr(dst + r0 * T1), &tm, (int)(r.j * T1), map_coord(pos, 1, r0, (int)r.t, 0),
+                           map_coord(pos, 2, r0, (int)r.t, 0), map_coord(pos, 3, r0, (int)r.t, 0), full);
+        } else {
+          mbar_arrive(full);
+        }
+        armed_tma[b] = true;
+        armed_par[b] = (it >> 1) & 1;
+      } else if (r.kind == 1) {
+        const float2* src = k.ring + (r.t % k.S) * N + r.j * T2 * N2;
+#pragma unroll 4
+        for (int c = lane; c < TP / 2; c += 32) cp_async16(dst + 2 * c, src + 2 * c);
+        cp_async_arrive(full);
+      } else {
+        mbar_arrive(full);  // an A item without tensor map (loaded by the compute warps), or the end
+      }
+      if (lane == 0) mbar_arrive(full);  // releases info[b] to the compute warps
+      pend[b] = r;
+      if (r.kind < 0) break;
+    }
+    if (!fail) {
+      // the end: publish the item still in the other buffer once it is done
+      const int o = (it & 1) ^ 1;
+      if (it >= 1 && __shfl_sync(0xffffffffu, (int)(pend[o].kind >= 0), 0)) {
+        if (mbar_wait(smem_addr(bars + 2 + o), ((it - 1) >> 1) & 1)) publish(o);
+        else fail = true;
+      }
+    }
+    if (fail) {
+      // a wait gave up: stop the compute warps at the item they wait for next
+      // (the one for buffer it & 1, not armed), then let copies in flight land
+      const int b = it & 1;
+      if (lane == 0) {
+        gb_set_status(k.status, kStatusTimeout);
+        info[b] = ItemSlot{0, 0, -2};
+      }
+      __syncwarp();
+      mbar_arrive(smem_addr(bars + b));
+      if (lane == 0) mbar_arrive(smem_addr(bars + b));
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      for (int x = 0; x < 2; ++x)
+        if (armed_tma[x]) mbar_wait(smem_addr(bars + x), armed_par[x]);
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------------- compute warps
   // pass A mapping: lanes across the T1 columns (tile loads and column stores)
   const int at = tid % T1, au = tid / T1;
   const int aj = tid / CA::TPT, auj = tid % CA::TPT;
   // pass B mapping: lanes along a row for the loads, across the T2 rows for the stores
   const int bj = tid / CB::TPT, buj = tid % CB::TPT;
   const int bt = tid % T2, bu = tid / T2;
-
-  auto item = [&](long long i) { return i < total ? decode(i, k.count, k.D, nA, nB) : ItemRef{-1, 0, 0}; };
-
-  if (tid == 0) {
-    for (int b = 0; b < 2; ++b)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    fetched[0] = (long long)atomicAdd(ctr, 1u);
-    fetched[1] = (long long)atomicAdd(ctr, 1u);
-  }
-  __syncthreads();
-
-  uint32_t ph0 = 0, ph1 = 0;
-  bool fly0 = false, fly1 = false;  // a box issued into buffer 0 / 1 and not yet waited for
-  bool bad = false;
-
-  // prefetch item `it` into buffer b: A -> TMA boxes (thread 0); B -> cp.async
-  // of its T2 rows (all threads; the caller has checked the dependency).
-  // Every thread commits exactly one cp.async group per call.
-  auto prefetch = [&](int b, const ItemRef& it) {
-    float2* dst = ibuf + b * TP;
-    if (it.kind == 0 && tmap_ok) {
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const uint32_t bar = smem_addr(bars + b);
-        expect_tx(bar, (uint32_t)(TP * 8));
-        constexpr int BOXR = N1 < 256 ? N1 : 256;
-#pragma unroll
-        for (int r0 = 0; r0 < N1; r0 += BOXR)
-          tensor_copy_4d(smem_addr(dst + r0 * T1), &tm, (int)(it.j * T1), map_coord(pos, 1, r0, (int)it.t, 0),
-                         map_coord(pos, 2, r0, (int)it.t, 0), map_coord(pos, 3, r0, (int)it.t, 0), bar);
-      }
-      (b ? fly1 : fly0) = true;
-    } else if (it.kind == 1) {
-      const float2* src = k.ring + (it.t % k.S) * N + it.j * T2 * N2;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int c = tid + q * NT;  // 16-byte chunk
-        cp_async16(dst + 2 * c, src + 2 * c);
-      }
-    }
-    cp_async_commit();
-  };
-
-  // A B item is prefetched only when the A items it reads are already done:
-  // the check never waits, because this CTA may itself hold one of them as
-  // its current item.  Otherwise its rows are loaded when it is processed,
-  // after a bounded wait.
-  auto inputs_done = [&](const ItemRef& it) -> int {
-    return it.kind != 1 || ld_acquire(doneA + it.t) >= (unsigned)nA;
-  };
-
-  ItemRef ci = item(fetched[0]);
-  if (tid == 0) ready[0] = inputs_done(ci);
-  __syncthreads();
-  bool cur_loaded = ready[0] != 0;
-  if (cur_loaded) prefetch(0, ci);
-  else cp_async_commit();
-  int buf = 0;
-  int slot3 = 1;  // fetched[slot3] holds the item after ci
   float2 v[16];
-  while (ci.kind >= 0) {
-    long long f2 = 0;
-    if (tid == 0) {
-      f2 = (long long)atomicAdd(ctr, 1u);  // two ahead: used at the end of this item
-      ready[0] = inputs_done(item(fetched[slot3]));  // thread 0 wrote fetched[slot3] itself
+  for (int it = 0;; ++it) {
+    const int b = it & 1;
+    if (!mbar_wait(smem_addr(bars + b), (it >> 1) & 1)) {
+      if (tid == 0) gb_set_status(k.status, kStatusTimeout);
+      break;
     }
-    __syncthreads();  // the other buffer was read by the previous item
-    const ItemRef ni = item(fetched[slot3]);
-    const bool next_loaded = ready[0] != 0;
-    if (next_loaded) prefetch(buf ^ 1, ni);
-    else cp_async_commit();
-    float2* slot = k.ring + (ci.t % k.S) * N;
-    const float2* tile = ibuf + buf * TP;
-    if (ci.kind == 0) {
+    const ItemSlot r = info[b];
+    if (r.kind < 0) break;
+    const float2* tile = ibuf + b * TP;
+    float2* slot = k.ring + (r.t % k.S) * N;
+    gb_bar<NT>();  // the previous item's exchange rows are read
+    if (r.kind == 0) {
       // ---- A(t, j): columns [j T1, (j+1) T1) of transform t into the slot
-      bool fine = true;
-      if (tmap_ok) fine = mbar_wait(smem_addr(bars + buf), (buf ? ph1 : ph0) & 1);
-      if (tid == 0 && ci.t >= k.S) fine = fine && wait_count(doneB + (ci.t - k.S), (unsigned)nB);
-      if (__syncthreads_or(!fine)) {
-        bad = true;
-        break;
-      }
-      if (tmap_ok) {
-        if (buf) {
-          ++ph1;
-          fly1 = false;
-        } else {
-          ++ph0;
-          fly0 = false;
-        }
-        stage_in<L1, 0, true, T1>(v, tile + at, k.tw1, au, k.conj);
-      } else {
-        stage_in<L1, 0, true, N2>(v, k.in + ci.t * k.vis + ci.j * T1 + at, k.tw1, au, k.conj);
-      }
-      const int64_t col = ci.j * T1 + at;  // l2
+      if (tmap_ok) stage_in<L1, 0, true, T1>(v, tile + at, k.tw1, au, k.conj);
+      else stage_in<L1, 0, true, N2>(v, k.in + r.t * k.vis + r.j * T1 + at, k.tw1, au, k.conj);
+      const int64_t col = r.j * T1 + at;  // l2
       stage_out_x<L1, 0>(v, xbuf + at * CA::PITCH, au);
-      __syncthreads();
-      later_stages<L1, 1, true>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, N2, k.tw1, auj, au,
-                                k.conj, true, k.ptwA, k.ptwB, col);
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) atomicAdd(doneA + ci.t, 1u);
+      gb_bar<NT>();
+      later_stages<L1, 1, true, false, NT>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, N2, k.tw1,
+                                           auj, au, k.conj, true, k.ptwA, k.ptwB, col);
     } else {
       // ---- B(t, j): rows [j T2, (j+1) T2) of the slot into Y[k1 + k2 n1]
-      if (cur_loaded) {
-        cp_async_wait1();  // this item's rows (the group before the next item's)
-      } else {
-        const int fine = tid == 0 ? (int)wait_count(doneA + ci.t, (unsigned)nA) : 1;
-        if (__syncthreads_or(!fine)) {
-          bad = true;
-          break;
-        }
-        prefetch(buf, ci);
-        cp_async_wait0();
-      }
-      __syncthreads();
-      if (tid == 0) {
-        // every read of these rows has landed: the slot may be rewritten
-        __threadfence();
-        atomicAdd(doneB + ci.t, 1u);
-      }
-      const int64_t row0 = ci.j * T2;
+      const int64_t row0 = r.j * T2;
       stage_in<L2, 0, true, 1>(v, tile + bj * N2, k.tw2, buj, k.conj);
       stage_out_x<L2, 0>(v, xbuf + bj * CB::PITCH, buj);
-      __syncthreads();
-      later_stages<L2, 1, false>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH, k.out + ci.t * k.vos + row0 + bt,
-                                 N1, k.tw2, buj, bu, k.conj, true, nullptr, nullptr, 0);
+      gb_bar<NT>();
+      later_stages<L2, 1, false, false, NT>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH,
+                                            k.out + r.t * k.vos + row0 + bt, N1, k.tw2, buj, bu, k.conj, true,
+                                            nullptr, nullptr, 0);
     }
-    if (tid == 0) fetched[(slot3 + 1) % 3] = f2;
-    slot3 = (slot3 + 1) % 3;
-    ci = ni;
-    cur_loaded = next_loaded;
-    buf ^= 1;
-  }
-  cp_async_wait0();
-  if (bad) {
-    // a wait gave up: let the boxes this CTA issued land (bounded) before it exits
-    if (fly0) mbar_wait(smem_addr(bars + 0), ph0 & 1);
-    if (fly1) mbar_wait(smem_addr(bars + 1), ph1 & 1);
-    if (tid == 0) gb_set_status(k.status, kStatusTimeout);
+    mbar_arrive(smem_addr(bars + 2 + b));  // this thread's stores are done
   }
 }
 
@@ -301,7 +334,7 @@ int grid_of() {
     return 0;
   }
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, G::TP / 16, G::smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, G::TP / 16 + 32, G::smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -334,7 +367,7 @@ cudaError_t launch(const GbL2FS& k, cudaStream_t st) {
   memset(&tm, 0, sizeof(tm));
   int pos = 0;
   const int tmap_ok = gb_p2_rows_map(g, G::T1, &tm, &pos);
-  gb_l2fs_kernel<L1, L2, G::TP, G::MINB><<<(unsigned)grid, G::TP / 16, G::smem, st>>>(k, tm, tmap_ok, pos);
+  gb_l2fs_kernel<L1, L2, G::TP, G::MINB><<<(unsigned)grid, G::TP / 16 + 32, G::smem, st>>>(k, tm, tmap_ok, pos);
   return cudaGetLastError();
 }
 

@@ -126,6 +126,48 @@ int canonicalize(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, i
   return FFT_OK;
 }
 
+// A real-data problem (sec. 5, sec. 7): N's last dimension is the real one;
+// on the complex side it has n / 2 + 1 entries.  Strides stay in the units of
+// each side.  Length-1 dimensions other than the last are dropped (the last
+// one is kept: a length-1 real transform is still a real-to-complex copy).
+int canonicalize_real(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, int kind, unsigned flags,
+                      Problem& P) {
+  if (rank < 1 || hr < 0 || !dims || (hr > 0 && !hd) || (kind != 1 && kind != 2)) return FFT_ERR_INVALID_ARG;
+  if (flags & ~kKnownFlags) return FFT_ERR_INVALID_ARG;
+  if (rank > 3 || hr > 3) return FFT_ERR_UNSUPPORTED;
+  if (flags & (FFT_INPLACE | FFT_EXTERNAL_SCRATCH | FFT_PREC_TC_FP16 | FFT_PREC_TC_BF16 | FFT_PREC_SPLIT))
+    return FFT_ERR_UNSUPPORTED;
+  P = Problem();
+  P.kind = kind;
+  P.sign = kind == 1 ? -1 : 1;
+  P.flags = flags;
+  for (int i = 0; i < rank; ++i) {
+    if (dims[i].n < 0) return FFT_ERR_INVALID_ARG;
+    if (dims[i].n == 0) P.empty = true;
+  }
+  for (int i = 0; i < hr; ++i) {
+    if (hd[i].n < 0) return FFT_ERR_INVALID_ARG;
+    if (hd[i].n == 0) P.empty = true;
+  }
+  if (P.empty) return FFT_OK;
+  for (int i = 0; i + 1 < rank; ++i)
+    if (dims[i].n > 1) P.N.push_back({dims[i].n, dims[i].is, dims[i].os});
+  P.N.push_back({dims[rank - 1].n, dims[rank - 1].is, dims[rank - 1].os});
+  for (int i = 0; i < hr; ++i)
+    if (hd[i].n > 1) P.V.push_back({hd[i].n, hd[i].is, hd[i].os});
+  // the output map must be injective (the complex side with n / 2 + 1 entries)
+  std::vector<Dim> all = P.N;
+  if (kind == 1) all.back().n = all.back().n / 2 + 1;
+  all.insert(all.end(), P.V.begin(), P.V.end());
+  std::sort(all.begin(), all.end(), [](const Dim& a, const Dim& b) { return iabs64(a.os) < iabs64(b.os); });
+  int64_t span = 0;
+  for (const Dim& d : all) {
+    if (d.n > 1 && iabs64(d.os) <= span) return FFT_ERR_OUTPUT_OVERLAP;
+    span += (d.n - 1) * iabs64(d.os);
+  }
+  return FFT_OK;
+}
+
 void footprint(const std::vector<Dim>& N, const std::vector<Dim>& V, bool input, int64_t* lo, int64_t* hi) {
   int64_t a = 0, b = 0;
   auto acc = [&](const Dim& d) {

@@ -68,6 +68,10 @@ _lib = None
 _SIGNATURES = {
     "fft_plan_dft": (ctypes.c_void_p, [ctypes.c_int, ctypes.POINTER(fft_iodim), ctypes.c_int,
                                        ctypes.POINTER(fft_iodim), ctypes.c_int, ctypes.c_uint]),
+    "fft_plan_dft_r2c": (ctypes.c_void_p, [ctypes.c_int, ctypes.POINTER(fft_iodim), ctypes.c_int,
+                                           ctypes.POINTER(fft_iodim), ctypes.c_uint]),
+    "fft_plan_dft_c2r": (ctypes.c_void_p, [ctypes.c_int, ctypes.POINTER(fft_iodim), ctypes.c_int,
+                                           ctypes.POINTER(fft_iodim), ctypes.c_uint]),
     "fft_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fft_destroy": (None, [ctypes.c_void_p]),
     "fft_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
@@ -165,6 +169,26 @@ def fft_plan_dft(dims, howmany=(), sign=-1, flags=0):
     p = load().fft_plan_dft(r, d, hr, h, int(sign), int(flags))
     if not p:
         raise GbfftError(fft_last_error(), "fft_plan_dft")
+    return p
+
+
+def fft_plan_dft_r2c(dims, howmany=(), flags=0):
+    """Plan a real-input DFT (real strides on the input side, complex on the output)."""
+    r, d = _dims(dims)
+    hr, h = _dims(howmany)
+    p = load().fft_plan_dft_r2c(r, d, hr, h, int(flags))
+    if not p:
+        raise GbfftError(fft_last_error(), "fft_plan_dft_r2c")
+    return p
+
+
+def fft_plan_dft_c2r(dims, howmany=(), flags=0):
+    """Plan a real-output DFT (complex strides on the input side, real on the output)."""
+    r, d = _dims(dims)
+    hr, h = _dims(howmany)
+    p = load().fft_plan_dft_c2r(r, d, hr, h, int(flags))
+    if not p:
+        raise GbfftError(fft_last_error(), "fft_plan_dft_c2r")
     return p
 
 

@@ -278,3 +278,20 @@ def test_plan_bluestein_store_epilogues():
         assert "bluestein n=10007 m=20160" in t and "pointwise Z = conj(A Bhat)" in t, t
     finally:
         gbfft.fft_forget_wisdom()
+
+
+def test_real_data_plan_validation():
+    """Real-data planners (sec. 5, 7) validate before touching a device."""
+    def code(fn, dims, how=(), flags=0):
+        with pytest.raises(gbfft.GbfftError) as e:
+            fn(dims, how, flags)
+        return e.value.code
+    r2c, c2r = gbfft.fft_plan_dft_r2c, gbfft.fft_plan_dft_c2r
+    assert code(r2c, []) == gbfft.FFT_ERR_INVALID_ARG                        # rank 0
+    assert code(r2c, [(8, 1, 1)], (), gbfft.FFT_INPLACE) == gbfft.FFT_ERR_UNSUPPORTED
+    assert code(c2r, [(8, 1, 1)], (), gbfft.FFT_PREC_TC_BF16) == gbfft.FFT_ERR_UNSUPPORTED
+    assert code(r2c, [(-1, 1, 1)]) == gbfft.FFT_ERR_INVALID_ARG
+    # r2c of n = 8 has 5 outputs per transform: a batch stride of 4 overlaps
+    assert code(r2c, [(8, 1, 1)], [(3, 8, 4)]) == gbfft.FFT_ERR_OUTPUT_OVERLAP
+    # c2r writes 8 reals per transform: stride 8 is fine, 7 overlaps
+    assert code(c2r, [(8, 1, 1)], [(3, 5, 7)]) == gbfft.FFT_ERR_OUTPUT_OVERLAP
