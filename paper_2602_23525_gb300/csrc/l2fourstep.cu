@@ -119,26 +119,25 @@ struct ItemSlot {
 };
 
 // TP points per item (T1 = TP / n1 columns, T2 = TP / n2 rows), 16 values a
-// compute thread, NT = TP / 16 compute threads plus one control warp.
-//   control warp: takes the next item from the device counter, waits
-//     (bounded) until its inputs are complete (B: the A items of its
-//     transform; A: the B items of the transform whose slot it rewrites),
+// compute thread, NT = TP / 16 compute threads plus two control warps, so
+// that no compute warp ever stalls on a global round trip:
+//   producer warp: takes the next item from the device counter (indices
+//     fetched two ahead), waits (bounded) until its inputs are complete,
 //     fills landing buffer b (A: tensor-map boxes; B: cp.async of the ring
-//     rows through L2) and arrives on full[b]; once the compute warps arrive
-//     on done[b] it publishes the finished item to the other CTAs (a
-//     gpu-scope fence, then the completion counter).  It alone stalls on
-//     global round trips.
+//     rows through L2) and arrives on full[b];
 //   compute warps: wait on full[b], compute the item's stages (named barrier
-//     1 among themselves), store, arrive on done[b].
+//     1 among themselves), store, arrive on done[b];
+//   publisher warp: after done[b], hands buffer b back (pub[b]) and publishes
+//     the item to the other CTAs (a gpu-scope fence, then the count).
 template <int L1, int L2, int TP, int MINB>
-__global__ void __launch_bounds__(TP / 16 + 32, MINB)
+__global__ void __launch_bounds__(TP / 16 + 64, MINB)
     gb_l2fs_kernel(const __grid_constant__ GbL2FS k, const __grid_constant__ CUtensorMap tm, int tmap_ok, int pos) {
   using CA = P2<L1>;
   using CB = P2<L2>;
   constexpr int N1 = CA::N, N2 = CB::N, T1 = TP / N1, T2 = TP / N2, NT = TP / 16;
   constexpr int64_t N = (int64_t)N1 * N2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                  // full[2], done[2]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                  // full[2], done[2], pub[2]
   ItemSlot* info = reinterpret_cast<ItemSlot*>(smem_raw + 64);             // 2 x 24 bytes
   float2* ibuf = reinterpret_cast<float2*>(smem_raw + 128);
   float2* xbuf = ibuf + 2 * TP;
@@ -148,60 +147,82 @@ __global__ void __launch_bounds__(TP / 16 + 32, MINB)
 
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
-      // full: one arrival per control lane (plain, with the expected bytes, or
+      // full: one arrival per producer lane (plain, with the expected bytes, or
       // when its cp.async copies land) plus lane 0's release of info[b]
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(33));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 2 + b)), "r"(NT));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 4 + b)), "r"(1));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  unsigned* ctr = k.sync;
+  unsigned* doneA = k.sync + 1;
+  unsigned* doneB = k.sync + 1 + k.count;
+
+  if (tid >= NT + 32) {
+    // ---------------------------------------------------------------- publisher warp
+    // after the compute warps finish item `it` (done[b]) it hands buffer b
+    // back to the producer (pub[b]), then publishes the item to the other
+    // CTAs: a gpu-scope fence (the compute warps' stores, ordered before
+    // their arrival on done[b], become visible first), then the count.
+    const int lane = tid - NT - 32;
+    for (int it = 0;; ++it) {
+      const int b = it & 1;
+      const uint32_t par = (it >> 1) & 1;
+      if (!mbar_wait(smem_addr(bars + b), par)) {
+        if (lane == 0) gb_set_status(k.status, kStatusTimeout);
+        break;
+      }
+      const ItemSlot r = info[b];
+      if (r.kind < 0) break;
+      if (!mbar_wait(smem_addr(bars + 2 + b), par)) {
+        if (lane == 0) gb_set_status(k.status, kStatusTimeout);
+        break;
+      }
+      if (lane == 0) {
+        mbar_arrive(smem_addr(bars + 4 + b));
+        __threadfence();
+        atomicAdd((r.kind == 0 ? doneA : doneB) + r.t, 1u);
+      }
+      __syncwarp();
+    }
+    return;
+  }
 
   if (tid >= NT) {
-    // ---------------------------------------------------------------- control warp
+    // ---------------------------------------------------------------- producer warp
+    // takes the next item (indices fetched two ahead), waits (bounded) until
+    // its inputs are complete -- B: the A items of its transform; A: the B
+    // items of the transform whose slot it rewrites -- and fills landing
+    // buffer b once the publisher has handed it back.
     const int lane = tid - NT;
-    unsigned* ctr = k.sync;
-    unsigned* doneA = k.sync + 1;
-    unsigned* doneB = k.sync + 1 + k.count;
-    ItemSlot pend[2] = {{0, 0, -1}, {0, 0, -1}};  // item in buffer b, not yet published
-    bool armed_tma[2] = {false, false};
-    uint32_t armed_par[2] = {0, 0};
-    // publish item pend[b] (lane 0): the compute warps' stores, ordered before
-    // their arrival on done[b], reach gpu scope before the completion count
-    auto publish = [&](int b) {
-      if (lane == 0 && pend[b].kind >= 0) {
-        __threadfence();
-        atomicAdd((pend[b].kind == 0 ? doneA : doneB) + pend[b].t, 1u);
-      }
-      pend[b].kind = -1;
-    };
-    // bounded wait (lane 0) until *c >= target.  The item this CTA computes
-    // in the other buffer may be one of those waited for: it is published as
-    // soon as the compute warps are done with it, inside the wait.
-    auto wait_dep = [&](const unsigned* c, unsigned target, int other, uint32_t other_par) -> bool {
-      const unsigned long long t0 = globaltimer();
-      while (ld_acquire(c) < target) {
-        if (pend[other].kind >= 0 && mbar_try(smem_addr(bars + 2 + other), other_par)) publish(other);
-        if (globaltimer() - t0 > kWaitLimitNs) return false;
-        __nanosleep(64);
-      }
-      return true;
-    };
+    long long f_a = 0, f_b = 0;
+    if (lane == 0) {
+      f_a = (long long)atomicAdd(ctr, 1u);
+      f_b = (long long)atomicAdd(ctr, 1u);
+    }
+    bool tma0 = false, tma1 = false;  // tensor-map boxes in flight into buffer 0 / 1
+    uint32_t tpar0 = 0, tpar1 = 0;
     bool fail = false;
     int it = 0;
     for (;; ++it) {
       const int b = it & 1;
-      const uint32_t full = smem_addr(bars + b), done = smem_addr(bars + 2 + b);
+      const uint32_t full = smem_addr(bars + b);
       if (it >= 2) {
-        if (!mbar_wait(done, ((it - 2) >> 1) & 1)) {
+        if (!mbar_wait(smem_addr(bars + 4 + b), ((it - 2) >> 1) & 1)) {
           fail = true;
           break;
         }
-        armed_tma[b] = false;
-        publish(b);  // unless published already during a dependency wait
+        if (b) tma1 = false;
+        else tma0 = false;
       }
       long long idx = 0;
-      if (lane == 0) idx = (long long)atomicAdd(ctr, 1u);
+      if (lane == 0) {
+        idx = f_a;
+        f_a = f_b;
+        f_b = (long long)atomicAdd(ctr, 1u);  // used two items from now
+      }
       idx = __shfl_sync(0xffffffffu, idx, 0);
       ItemSlot r{0, 0, -1};
       if (idx < total) {
@@ -210,10 +231,8 @@ __global__ void __launch_bounds__(TP / 16 + 32, MINB)
       }
       int ok = 1;
       if (lane == 0) {
-        const int o = b ^ 1;
-        const uint32_t op = ((it - 1) >> 1) & 1;  // phase of the other buffer's item (it - 1)
-        if (r.kind == 1) ok = wait_dep(doneA + r.t, (unsigned)nA, o, op);
-        else if (r.kind == 0 && r.t >= k.S) ok = wait_dep(doneB + (r.t - k.S), (unsigned)nB, o, op);
+        if (r.kind == 1) ok = wait_count(doneA + r.t, (unsigned)nA);
+        else if (r.kind == 0 && r.t >= k.S) ok = wait_count(doneB + (r.t - k.S), (unsigned)nB);
         info[b] = r;
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) {
@@ -234,8 +253,13 @@ __global__ void __launch_bounds__(TP / 16 + 32, MINB)
         } else {
           mbar_arrive(full);
         }
-        armed_tma[b] = true;
-        armed_par[b] = (it >> 1) & 1;
+        if (b) {
+          tma1 = true;
+          tpar1 = (it >> 1) & 1;
+        } else {
+          tma0 = true;
+          tpar0 = (it >> 1) & 1;
+        }
       } else if (r.kind == 1) {
         const float2* src = k.ring + (r.t % k.S) * N + r.j * T2 * N2;
 #pragma unroll 4
@@ -244,21 +268,12 @@ __global__ void __launch_bounds__(TP / 16 + 32, MINB)
       } else {
         mbar_arrive(full);  // an A item without tensor map (loaded by the compute warps), or the end
       }
-      if (lane == 0) mbar_arrive(full);  // releases info[b] to the compute warps
-      pend[b] = r;
+      if (lane == 0) mbar_arrive(full);  // releases info[b] to the compute and publisher warps
       if (r.kind < 0) break;
     }
-    if (!fail) {
-      // the end: publish the item still in the other buffer once it is done
-      const int o = (it & 1) ^ 1;
-      if (it >= 1 && __shfl_sync(0xffffffffu, (int)(pend[o].kind >= 0), 0)) {
-        if (mbar_wait(smem_addr(bars + 2 + o), ((it - 1) >> 1) & 1)) publish(o);
-        else fail = true;
-      }
-    }
     if (fail) {
-      // a wait gave up: stop the compute warps at the item they wait for next
-      // (the one for buffer it & 1, not armed), then let copies in flight land
+      // a wait gave up: stop the compute and publisher warps at the item they
+      // wait for next (buffer it & 1, not armed), then let copies in flight land
       const int b = it & 1;
       if (lane == 0) {
         gb_set_status(k.status, kStatusTimeout);
@@ -268,8 +283,8 @@ __global__ void __launch_bounds__(TP / 16 + 32, MINB)
       mbar_arrive(smem_addr(bars + b));
       if (lane == 0) mbar_arrive(smem_addr(bars + b));
       asm volatile("cp.async.wait_all;" ::: "memory");
-      for (int x = 0; x < 2; ++x)
-        if (armed_tma[x]) mbar_wait(smem_addr(bars + x), armed_par[x]);
+      if (tma0) mbar_wait(smem_addr(bars + 0), tpar0);
+      if (tma1) mbar_wait(smem_addr(bars + 1), tpar1);
     }
     return;
   }
@@ -334,7 +349,7 @@ int grid_of() {
     return 0;
   }
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, G::TP / 16 + 32, G::smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, G::TP / 16 + 64, G::smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -367,7 +382,7 @@ cudaError_t launch(const GbL2FS& k, cudaStream_t st) {
   memset(&tm, 0, sizeof(tm));
   int pos = 0;
   const int tmap_ok = gb_p2_rows_map(g, G::T1, &tm, &pos);
-  gb_l2fs_kernel<L1, L2, G::TP, G::MINB><<<(unsigned)grid, G::TP / 16 + 32, G::smem, st>>>(k, tm, tmap_ok, pos);
+  gb_l2fs_kernel<L1, L2, G::TP, G::MINB><<<(unsigned)grid, G::TP / 16 + 64, G::smem, st>>>(k, tm, tmap_ok, pos);
   return cudaGetLastError();
 }
 
