@@ -201,7 +201,9 @@ extern "C" int fft_import_wisdom(const char* text) {
     if (tab == std::string::npos || tab == 0 || tab + 1 >= line.size()) return set_err(FFT_ERR_WISDOM);
     const std::string key = line.substr(0, tab), val = line.substr(tab + 1);
     if (key.rfind("r1 ", 0) != 0) return set_err(FFT_ERR_WISDOM);
-    if (val == "p2" || val == "mr" || val == "xpose") {
+    if (val == "p2" || val == "mr" || val == "xpose" || val == "indirect") {
+    } else if (val.rfind("ip4:", 0) == 0) {
+      if (atoll(val.c_str() + 4) < 2) return set_err(FFT_ERR_WISDOM);
     } else if (val.rfind("single:", 0) == 0) {
       PassCfg c;
       if (!c.parse(val.substr(7))) return set_err(FFT_ERR_WISDOM);

@@ -200,14 +200,55 @@ struct Builder {
 
   // ---------------------------------------------------------------- steps
 
+  // the in-place rank-0 problems this library solves (sec. 4.2, rank-0 plans):
+  // the identity, and a square transpose -- two dims of equal length with
+  // their input and output strides swapped -- batched over dims with equal
+  // strides.  Returns 0 none (identity), 1 transpose, -1 unsupported.
+  static int inplace_permutation(const std::vector<Dim>& V, int* a, int* b) {
+    int pa = -1, pb = -1;
+    for (int i = 0; i < (int)V.size(); ++i) {
+      if (V[i].is == V[i].os || V[i].n == 1) continue;
+      if (pa < 0) pa = i;
+      else if (pb < 0) pb = i;
+      else return -1;
+    }
+    if (pa < 0) return 0;
+    if (pb < 0) return -1;
+    const Dim& x = V[pa];
+    const Dim& y = V[pb];
+    if (x.n != y.n || x.is != y.os || x.os != y.is) return -1;  // non-square in place: not built
+    *a = pa;
+    *b = pb;
+    return 1;
+  }
+
   void emit_copy(const std::vector<Dim>& V, int src, int dst, int depth) {
     if (src == dst) {
-      for (const Dim& d : V)
-        if (d.is != d.os) {
-          err = FFT_ERR_UNSUPPORTED;  // in-place rank-0 transposes are not built
-          return;
-        }
-      line(depth, "copy in place: nothing to do");
+      int a = -1, b = -1;
+      const int kind = inplace_permutation(V, &a, &b);
+      if (kind < 0 || (int)V.size() > GB_MAX_VDIMS) {
+        err = FFT_ERR_UNSUPPORTED;  // a non-square in-place transpose
+        return;
+      }
+      if (kind == 0) {
+        line(depth, "copy in place: nothing to do");
+        return;
+      }
+      Step s;
+      s.kind = STEP_TRANSPOSE_IP;
+      s.src = src;
+      s.dst = dst;
+      s.copy.nv = (int)V.size();
+      s.copy.total = 1;
+      for (int i = 0; i < (int)V.size(); ++i) {
+        s.copy.vn[i] = V[i].n;
+        s.copy.vis[i] = V[i].is;
+        s.copy.vos[i] = V[i].os;
+        s.copy.total *= V[i].n;
+      }
+      P->steps.push_back(s);
+      line(depth, "transpose in place " + std::to_string(V[a].n) + " x " + std::to_string(V[b].n) +
+                      " (32 x 32 tile pairs swapped through shared memory) vdims=" + dims_str(V));
       return;
     }
     if ((int)V.size() > GB_MAX_VDIMS) {
@@ -1290,6 +1331,54 @@ struct Builder {
     line(depth + 1, "pointwise Y[0] = x0 + dc, Y[g^-q] = x0 + conj(D[q])");
   }
 
+  // ---------------------------------------------------------------- in place
+  // An in-place transform of n = s^2 contiguous points without scratch (sec.
+  // 4.2, in-place plans from DIT/DIF steps and in-place transposes): the
+  // column DFTs of the s x s matrix in place, each CTA loading its whole
+  // column tile before writing it back (twiddle w_n^{l2 k1} fused), the row
+  // DFTs in place, then an in-place square transpose puts Y[k1 + s k2] in
+  // natural order.
+  bool ip4_ok(const Dim& d, const std::vector<Dim>& V, int64_t s) const {
+    const int e = log2_exact(s);
+    if (prec || e < 6 || e > 12 || s * s != d.n || d.is != 1 || d.os != 1 || V.size() > 1) return false;
+    return V.empty() || V[0].is == V[0].os;
+  }
+
+  void emit_ip4(const Dim& d, const std::vector<Dim>& V, int buf, int conj, int64_t s, int depth) {
+    if (!ip4_ok(d, V, s)) {
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    const int64_t n = d.n, count = V.empty() ? 1 : V[0].n, vs = V.empty() ? n : V[0].is;
+    line(depth, "cooley-tukey n=" + std::to_string(n) + " = " + std::to_string(s) + " x " + std::to_string(s) +
+                    " in place without scratch (columns, rows, square transpose)");
+    std::vector<Dim> V1{{s, 1, 1}}, V2{{s, s, s}};
+    if (count > 1) {
+      V1.push_back({count, vs, vs});
+      V2.push_back({count, vs, vs});
+    }
+    emit_p2({s, s, s}, canon_vec(V1), buf, buf, conj, n, depth + 1);
+    if (err) return;
+    emit_p2({s, 1, 1}, canon_vec(V2), buf, buf, conj, 0, depth + 1);  // rows and batch merge into one loop
+    if (err) return;
+    std::vector<Dim> T{{s, s, 1}, {s, 1, s}};
+    if (count > 1) T.push_back({count, vs, vs});
+    emit_copy(T, buf, buf, depth + 1);
+  }
+
+  // The indirect plan of sec. 4.2: the data first rearranged into the output's
+  // layout (a rank-0 copy), then the transform solved in place there.
+  void emit_indirect(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int depth) {
+    line(depth, "indirect: copy into the output's layout, then the transform in place");
+    std::vector<Dim> all = V;
+    all.push_back(d);
+    emit_copy(canon_vec(all), src, dst, depth + 1);
+    if (err) return;
+    std::vector<Dim> Vo;
+    for (const Dim& v : V) Vo.push_back({v.n, v.os, v.os});
+    solve_rank1({d.n, d.os, d.os}, Vo, dst, dst, conj, depth + 1);
+  }
+
   // ---------------------------------------------------------------- real data
   // DFTs of real data (sec. 5, sec. 7), built from the complex plans above and
   // the pointwise steps of real.cu.  `loops` are the vector loops of the 1-D
@@ -1486,9 +1575,18 @@ struct Builder {
     return o.str();
   }
 
-  std::vector<std::string> candidates(const Dim& d, const std::vector<Dim>& V) {
+  std::vector<std::string> candidates(const Dim& d, const std::vector<Dim>& V, bool inplace = false) {
     std::vector<std::string> c;
     const int64_t n = d.n;
+    // a caller's in-place problem (not the in-place sub-problems of other
+    // plans): in estimate mode the scratch-free forms come first, since memory
+    // is why a caller asks for in place; measure mode times them with the rest
+    const bool caller_inplace = inplace && P->inplace;
+    const bool no_scratch_first = caller_inplace && !measure;
+    int64_t ip4_s = 1;
+    while (ip4_s * ip4_s < n) ip4_s <<= 1;
+    const bool ip4 = inplace && log2_exact(n) >= 14 && ip4_ok(d, V, ip4_s);
+    if (ip4 && caller_inplace) c.push_back("ip4:" + std::to_string(ip4_s));
     Dim v0{1, 0, 0};
     bool has_v = false;
     if (!V.empty()) {
@@ -1511,7 +1609,7 @@ struct Builder {
     // estimate mode: transforms of 2^12 and more down the columns of a
     // row-major array take the four-step with the columns innermost (two
     // passes of 64-column tiles beat one pass of two-column tiles when measured)
-    if (!prec && !measure && d.is != 1 && log2_exact(n) >= 12) {
+    if (!prec && !measure && !no_scratch_first && d.is != 1 && log2_exact(n) >= 12) {
       const int64_t a = estimate_split(n);
       bool unit = false;
       for (const Dim& v : V) unit = unit || (v.is == 1 && v.os == 1 && v.n % 64 == 0);
@@ -1610,6 +1708,13 @@ struct Builder {
       }
     }
     if (xpose && measure) c.push_back("xpose");
+    if (ip4 && measure) c.push_back("ip4:" + std::to_string(ip4_s));
+    // the indirect plan (sec. 4.2): copy into the output's layout, transform in place
+    if (measure && !inplace && !prec) {
+      bool differs = d.is != d.os;
+      for (const Dim& v : V) differs = differs || v.is != v.os;
+      if (differs) c.push_back("indirect");
+    }
     // Rader for a prime length: estimate mode takes it first where p - 1 is
     // smooth (one FFT of length p - 1 each way, against Bluestein's two of
     // length >= 2p - 1) unless p is small enough for the one-CTA fused
@@ -1682,7 +1787,7 @@ struct Builder {
       err = FFT_ERR_WISDOM;
       return "";
     }
-    std::vector<std::string> cands = candidates(d, V);
+    std::vector<std::string> cands = candidates(d, V, inplace);
     if (!measure || !device || cands.size() == 1) {
       if (measure && device) wisdom_put(key, cands[0]);
       return cands[0];
@@ -1738,6 +1843,18 @@ struct Builder {
         return;
       }
       emit_fourstep(d, V, src, dst, conj, n1, depth);
+    } else if (choice.rfind("ip4:", 0) == 0) {
+      if (src != dst) {
+        err = FFT_ERR_WISDOM;
+        return;
+      }
+      emit_ip4(d, V, dst, conj, atoll(choice.c_str() + 4), depth);
+    } else if (choice == "indirect") {
+      if (src == dst) {
+        err = FFT_ERR_WISDOM;
+        return;
+      }
+      emit_indirect(d, V, src, dst, conj, depth);
     } else if (choice.rfind("l2fs:", 0) == 0) {
       emit_l2fs(d, V, src, dst, conj, atoll(choice.c_str() + 5), depth);
     } else if (choice.rfind("rader:", 0) == 0) {
@@ -1880,6 +1997,13 @@ int launch_step(const Step& s, float2* const* bufs, cudaStream_t st) {
       k.ring = bufs[s.aux];
       k.sync = reinterpret_cast<unsigned*>(k.ring + k.S * ((int64_t)1 << (k.logn1 + k.logn2)));
       e = gb_launch_l2fs(k, st);
+      break;
+    }
+    case STEP_TRANSPOSE_IP: {
+      GbCopy c = s.copy;
+      c.in = bufs[s.dst];
+      c.out = bufs[s.dst];
+      e = gb_launch_transpose_inplace(c, st);
       break;
     }
     case STEP_R2C_POST: e = gb_launch_r2c_post(s.real, bufs[s.dst], st); break;

@@ -10,6 +10,9 @@
 cudaError_t gb_launch_pass(const GbPass& p, const GbPass* dev, const float2* in, float2* out, int threads,
                            size_t smem, int64_t grid, cudaStream_t st);
 cudaError_t gb_launch_copy(const GbCopy& c, cudaStream_t st);
+// in place (c.in == c.out): a square transpose of two dims whose input and
+// output strides are swapped, batched over dims with equal strides
+cudaError_t gb_launch_transpose_inplace(const GbCopy& c, cudaStream_t st);
 int gb_pass_max_smem_optin(void);
 
 // Power-of-two pass kernels with TMA tile loads (stockham_pow2.cu),

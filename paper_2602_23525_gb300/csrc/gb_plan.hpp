@@ -54,7 +54,8 @@ enum StepKind {
   STEP_R2C_PROMOTE = 14, // real input widened to complex
   STEP_C2R_PRE = 15,     // real output: the half-length complex input of the backward DFT
   STEP_C2R_EXPAND = 16,  // half spectrum extended to the full conjugate-symmetric spectrum
-  STEP_C2R_REAL = 17     // real parts to the real output
+  STEP_C2R_REAL = 17,    // real parts to the real output
+  STEP_TRANSPOSE_IP = 18 // in-place square transpose (rank 0, I = O)
 };
 
 // Buffer ids used by steps: 0 = user input, 1 = user output, 2+k = scratch k.

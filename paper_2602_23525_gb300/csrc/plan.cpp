@@ -85,9 +85,11 @@ int canonicalize(int rank, const fft_iodim* dims, int hr, const fft_iodim* hd, i
     if (hd[i].n == 0) P.empty = true;
   }
   if (flags & FFT_INPLACE) {
+    // a transform in place needs equal strides; a rank-0 problem in place is
+    // a permutation (sec. 4.1.1), which the planner accepts or refuses
     for (int i = 0; i < rank; ++i)
       if (dims[i].is != dims[i].os) return FFT_ERR_INPLACE_MISMATCH;
-    for (int i = 0; i < hr; ++i)
+    for (int i = 0; i < hr && rank > 0; ++i)
       if (hd[i].is != hd[i].os) return FFT_ERR_INPLACE_MISMATCH;
   }
   if (P.empty) return FFT_OK;

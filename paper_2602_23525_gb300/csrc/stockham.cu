@@ -58,7 +58,75 @@ __global__ void __launch_bounds__(256) gb_transpose_kernel(const GbCopy c, int d
   }
 }
 
+// In-place square transpose (the rank-0 problem of sec. 4.1.1 with I = O:
+// dims da, db of equal length s whose input and output strides are swapped;
+// every other dimension a batch loop with equal strides).  Element (i, j) at
+// i sa + j sb moves to j sa + i sb.  A block takes one pair of 32 x 32 tiles
+// (ti, tj), ti <= tj, of one batch index: both tiles are read into shared
+// memory before either is written back into the other's place (a diagonal
+// tile is transposed onto itself), so no element is overwritten before it
+// is read, and pairs are disjoint.
+__global__ void __launch_bounds__(256) gb_transpose_inplace_kernel(const GbCopy c, int da, int db) {
+  __shared__ float2 A[32][33], B[32][33];
+  float2* x = c.out;
+  const int64_t s = c.vn[da], sa = c.vis[da], sb = c.vis[db];
+  const int64_t T = (s + 31) / 32, npairs = T * (T + 1) / 2;
+  const int64_t nrest = c.total / (s * s);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int64_t t = blockIdx.x; t < npairs * nrest; t += gridDim.x) {
+    int64_t pair = t % npairs, rest = t / npairs, off = 0;
+    for (int d = c.nv - 1; d >= 0; --d) {
+      if (d == da || d == db) continue;
+      const int64_t q = rest / c.vn[d], k = rest - q * c.vn[d];
+      rest = q;
+      off += k * c.vis[d];
+    }
+    int64_t ti = 0;
+    while (pair >= T - ti) {  // upper triangle, row by row
+      pair -= T - ti;
+      ++ti;
+    }
+    const int64_t tj = ti + pair;
+#pragma unroll
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t i = ti * 32 + k, j = tj * 32 + tx;
+      if (i < s && j < s) A[k][tx] = x[off + i * sa + j * sb];
+      const int64_t i2 = tj * 32 + k, j2 = ti * 32 + tx;
+      if (ti != tj && i2 < s && j2 < s) B[k][tx] = x[off + i2 * sa + j2 * sb];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = ty; k < 32; k += 8) {
+      // row tj*32 + k, column ti*32 + tx receives element (ti*32 + tx, tj*32 + k) of tile A
+      const int64_t i = tj * 32 + k, j = ti * 32 + tx;
+      if (i < s && j < s) x[off + i * sa + j * sb] = A[tx][k];
+      const int64_t i2 = ti * 32 + k, j2 = tj * 32 + tx;
+      if (ti != tj && i2 < s && j2 < s) x[off + i2 * sa + j2 * sb] = B[tx][k];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t gb_launch_transpose_inplace(const GbCopy& c, cudaStream_t st) {
+  if (c.total <= 0) return cudaSuccess;
+  int da = -1, db = -1;
+  for (int a = 0; a < c.nv && da < 0; ++a)
+    for (int b = 0; b < c.nv; ++b)
+      if (a != b && c.vn[a] == c.vn[b] && c.vn[a] > 1 && c.vis[a] == c.vos[b] && c.vos[a] == c.vis[b] &&
+          c.vis[a] != c.vos[a]) {
+        da = a;
+        db = b;
+        break;
+      }
+  if (da < 0 || c.in != c.out) return cudaErrorInvalidValue;
+  const int64_t T = (c.vn[da] + 31) / 32;
+  const int64_t tiles = T * (T + 1) / 2 * (c.total / (c.vn[da] * c.vn[da]));
+  const int64_t blocks = tiles < 152 * 8 ? tiles : 152 * 8;
+  gb_transpose_inplace_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, da, db);
+  return cudaGetLastError();
+}
 
 int gb_pass_max_smem_optin(void) {
   int dev = 0, v = 0;

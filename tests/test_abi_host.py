@@ -295,3 +295,29 @@ def test_real_data_plan_validation():
     assert code(r2c, [(8, 1, 1)], [(3, 8, 4)]) == gbfft.FFT_ERR_OUTPUT_OVERLAP
     # c2r writes 8 reals per transform: stride 8 is fine, 7 overlaps
     assert code(c2r, [(8, 1, 1)], [(3, 5, 7)]) == gbfft.FFT_ERR_OUTPUT_OVERLAP
+
+
+def test_in_place_plans_without_scratch():
+    """In place (sec. 4.2): n = s^2 as columns, rows and an in-place square
+    transpose; rank-0 in-place square transposes; non-square refused."""
+    IP = gbfft.FFT_INPLACE
+    t = explain([(1 << 20, 1, 1)], [(4, 1 << 20, 1 << 20)], -1, IP)
+    assert "1024 x 1024 in place without scratch" in t
+    assert "load=rows store=cols" in t and "transpose in place 1024 x 1024" in t
+    t = explain([(4096, 4096, 4096), (4096, 1, 1)], [], -1, IP)
+    assert "cooley-tukey" not in t and t.count("pass p2-tma") == 2
+    t = explain([], [(64, 64, 1), (64, 1, 64), (3, 4096, 4096)], -1, IP)
+    assert "transpose in place 64 x 64" in t
+    assert explain_err([], [(64, 32, 1), (32, 1, 64)], -1, IP) == gbfft.FFT_ERR_UNSUPPORTED
+    # a transform in place still needs equal strides
+    assert explain_err([(64, 1, 2)], [], -1, IP) == gbfft.FFT_ERR_INPLACE_MISMATCH
+
+
+def test_indirect_plan_from_wisdom():
+    gbfft.fft_forget_wisdom()
+    try:
+        gbfft.fft_import_wisdom("gbfft-wisdom 1\nr1 n=4096 is=64 os=1 v=[(64,1,4096)] ip=0\tindirect\n")
+        t = explain([(4096, 64, 1)], [(64, 1, 4096)])
+        assert "indirect: copy into the output's layout" in t and "copy (rank-0)" in t
+    finally:
+        gbfft.fft_forget_wisdom()
