@@ -403,12 +403,21 @@ constexpr int tile_T(int logn, int load, int store) {
 }
 
 constexpr int min_blocks(int logn, int load, int store) {
-  return (load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG) ? (logn <= 12 ? 2 : 1) : (logn <= 8 ? 2 : 1);
+  return (load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG)
+             ? (logn >= 9 && logn <= 12 ? 3 : (logn <= 12 ? 2 : 1))
+             : (logn <= 8 ? 2 : 1);
+}
+
+// landing buffers per CTA: contiguous passes of 2^9..2^12 points keep one, so
+// that three CTAs fit an SM (their exchange rows and one 32 KB tile each)
+constexpr int land_bufs(int logn, int load, int store) {
+  return (load == GB_P2_LOAD_CONTIG && store == GB_P2_STORE_CONTIG && logn >= 9 && logn <= 12) ? 1 : 2;
 }
 
 template <int LOGN, int LOAD, int STORE, bool POSTTW, bool PW = false>
 cudaError_t launch_n(const GbP2& k, cudaStream_t st) {
-  return launch<LOGN, tile_T(LOGN, LOAD, STORE), 2, min_blocks(LOGN, LOAD, STORE), LOAD, STORE, POSTTW, PW>(k, st);
+  return launch<LOGN, tile_T(LOGN, LOAD, STORE), land_bufs(LOGN, LOAD, STORE), min_blocks(LOGN, LOAD, STORE), LOAD,
+                STORE, POSTTW, PW>(k, st);
 }
 
 // the store epilogue: contiguous transforms in, column tiles out (the last
