@@ -1699,8 +1699,11 @@ struct Builder {
         if (a > 1) {
           c.push_back("split:" + std::to_string(a));
           if (measure) {
-            for (int64_t b : {(int64_t)16, (int64_t)64, (int64_t)256, (int64_t)1024}) {
-              if (b != a && n % b == 0 && n / b > 1 && smooth_codelet(n / b) && b * b <= n * 4)
+            // every power-of-two column length 16..4096 whose row length is at
+            // least 16 (non-square splits often win: wider column tiles on one
+            // side, a one-pass row length on the other)
+            for (int64_t b = 16; b <= 4096; b *= 2) {
+              if (b != a && n % b == 0 && n / b >= 16 && smooth_codelet(n / b))
                 c.push_back("split:" + std::to_string(b));
             }
           }
