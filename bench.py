@@ -401,8 +401,10 @@ def time_oracle(sample):
 
 
 def cpu_baseline(budget_s=20.0):
-    flops, dt, threads = time_oracle(cpu_sample())
-    desc = ", ".join(f"{c} x n={n}" for n, c in cpu_sample())
+    # three times the base sample: about 12 s of oracle work on the 16 host cores
+    sample = cpu_sample(3.0)
+    flops, dt, threads = time_oracle(sample)
+    desc = ", ".join(f"{c} x n={n}" for n, c in sample)
     return {"value": round(flops / dt / 1e9, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
             "sample": f"forward transforms {desc} (oracle: direct eq. (1) for n<=4096, recursive "
                       f"Cooley-Tukey above), {dt:.1f} s", "seconds": round(dt, 2)}
@@ -633,6 +635,73 @@ def run_planner(args):
             "forward", "reps": reps, "estimate_penalty": pen, "sizes_3600_3840_4096": e2, "prime_plans": primes}
 
 
+def run_forms(args):
+    """The transform forms beyond the complex sweep, on one GPU: real-input (r2c)
+    and real-output (c2r) transforms of 2^26 real values (the half spectrum on the
+    complex side), and in-place complex transforms of 2^26 points planned without
+    scratch against the same problem out of place; CUDA events, forward unless
+    stated."""
+    import torch
+
+    from paper_2602_23525_gb300 import gbfft
+    total = 1 << 26
+    s = torch.cuda.current_stream().cuda_stream
+    reps = max(5, args.steps)
+
+    def timed(plan, a, b):
+        for _ in range(3):
+            gbfft.fft_execute(plan, a.data_ptr(), b.data_ptr(), s)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gbfft.fft_execute(plan, a.data_ptr(), b.data_ptr(), s)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    xr = torch.from_numpy(np.random.default_rng(fft_inputs.seed_for(9)).uniform(-1, 1, total)
+                          .astype(np.float32)).cuda()
+    out = []
+    for e in (12, 16, 20):
+        n = 1 << e
+        b = total // n
+        h = n // 2 + 1
+        yc = torch.empty(h * b, dtype=torch.complex64, device="cuda")
+        zr = torch.empty(total, dtype=torch.float32, device="cuda")
+        pf = gbfft.fft_plan_dft_r2c([(n, 1, 1)], [(b, n, h)], gbfft.FFT_MEASURE)
+        pb = gbfft.fft_plan_dft_c2r([(n, 1, 1)], [(b, h, n)], gbfft.FFT_MEASURE)
+        for kind, plan, a, c in (("r2c", pf, xr, yc), ("c2r", pb, yc, zr)):
+            ms = timed(plan, a, c)
+            out.append({"form": kind, "n": n, "batch": b, "ms": round(ms, 4),
+                        "gflops": round(2.5 * n * math.log2(n) * b / (ms * 1e-3) / 1e9, 1),
+                        "gbs_algorithmic": round(gbfft.fft_plan_bytes(plan) / (ms * 1e-3) / 1e9, 1),
+                        "launches": gbfft.fft_plan_launches(plan)})
+            gbfft.fft_destroy(plan)
+        del yc, zr
+    del xr
+    x = torch.from_numpy(fft_inputs.uniform_c64(total, fft_inputs.seed_for(10))).cuda()
+    y = torch.empty_like(x)
+    for e in (16, 20, 24):
+        n = 1 << e
+        b = total // n
+        how = [(b, n, n)] if b > 1 else []
+        pi = gbfft.Plan([(n, 1, 1)], how, -1, gbfft.FFT_INPLACE | gbfft.FFT_ESTIMATE)
+        po = gbfft.Plan([(n, 1, 1)], how, -1, gbfft.FFT_ESTIMATE)
+        ms_i = timed(pi.handle, x, x)
+        ms_o = timed(po.handle, x, y)
+        out.append({"form": "in place, no scratch", "n": n, "batch": b, "ms": round(ms_i, 4),
+                    "gflops": round(flops_of(n, b) / (ms_i * 1e-3) / 1e9, 1),
+                    "scratch_bytes": gbfft.fft_plan_scratch_bytes(pi.handle), "launches": pi.launches,
+                    "out_of_place_ms": round(ms_o, 4),
+                    "out_of_place_scratch_bytes": gbfft.fft_plan_scratch_bytes(po.handle)})
+        pi.destroy()
+        po.destroy()
+    return {"metric": METRIC, "unit": "GFLOP/s", "workload": "transform forms: real data and in place, "
+            "2^26 values per problem", "reps": reps, "forms": out}
+
+
 def _smooth7(m):
     for q in (2, 3, 5, 7):
         while m % q == 0:
@@ -694,7 +763,7 @@ def run_serving(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "uneven", "serving", "precision", "planner"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "uneven", "serving", "precision", "planner", "forms"],
                     help="sweep: the benchmark step; uneven / serving: extra workloads (their own line)")
     ap.add_argument("--requests", type=int, default=100000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: 0.7 x capacity)")
@@ -713,10 +782,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     args.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload in ("uneven", "serving", "precision", "planner"):
+    if args.workload in ("uneven", "serving", "precision", "planner", "forms"):
         if rank == 0:
             fn = {"uneven": run_uneven, "serving": run_serving, "precision": run_precision,
-                  "planner": run_planner}[args.workload]
+                  "planner": run_planner, "forms": run_forms}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":
