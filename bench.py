@@ -401,8 +401,8 @@ def time_oracle(sample):
 
 
 def cpu_baseline(budget_s=20.0):
-    # three times the base sample: about 12 s of oracle work on the 16 host cores
-    sample = cpu_sample(3.0)
+    # eight times the base sample: about 10-15 s of oracle work on 16 host cores
+    sample = cpu_sample(8.0)
     flops, dt, threads = time_oracle(sample)
     desc = ", ".join(f"{c} x n={n}" for n, c in sample)
     return {"value": round(flops / dt / 1e9, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
