@@ -1127,9 +1127,13 @@ struct Builder {
   // The four-step of eq. (2) as one persistent kernel whose intermediate stays
   // in an L2-resident ring (l2fourstep.cu): contiguous power-of-two transforms
   // of 2^14 .. 2^22 points, at most one vector loop.  The lag D between the A
-  // and B items of a transform is two waves of the persistent grid; the ring
-  // holds S = 2D transforms within kL2RingBytes (S > D is required).
+  // and B items of a transform is kL2Lag items per CTA of the persistent grid
+  // (a CTA holds up to four items at once: two claimed, two in its buffers;
+  // with a lag of two the B items waited on their A items for a fifth of the
+  // time, measured); the ring holds S = 2D transforms within kL2RingBytes
+  // (S > D is required).
   static constexpr int64_t kL2RingBytes = (int64_t)64 << 20;
+  static constexpr int64_t kL2Lag = 5;
 
   bool l2fs_shape(const Dim& d, const std::vector<Dim>& V, int64_t n1, int* l1, int* l2, int64_t* count,
                   int64_t* vis, int64_t* vos) const {
@@ -1151,7 +1155,7 @@ struct Builder {
     const int64_t per_t = ((int64_t)1 << l2) / T1 + ((int64_t)1 << l1) / T2;  // items per transform
     int64_t grid = device ? gb_l2fs_grid(l1, l2) : 0;
     if (grid <= 0) grid = (T1 << l1) <= 4096 ? 304 : 152;
-    int64_t d = std::max<int64_t>(1, (2 * grid + per_t - 1) / per_t);
+    int64_t d = std::max<int64_t>(1, (kL2Lag * grid + per_t - 1) / per_t);
     int64_t s = 2 * d;
     const int64_t cap = std::max<int64_t>(1, kL2RingBytes / (n * 8));
     if (s > cap) s = cap;
@@ -1621,8 +1625,25 @@ struct Builder {
       if (pc.prec) return c;  // the requested tensor-core precision decides the pass
     }
     const int lg = log2_exact(n);
-    // estimate mode takes the first candidate: the cluster pass where it beat
-    // two TMA passes when measured (2^14), the two passes above
+    // the four-step with its intermediate in L2 (one HBM round trip)
+    bool l2fs_ok = false, l2fs_busy = false;
+    const int64_t l2fs_n1 = lg >= 0 ? ((int64_t)1 << (lg / 2)) : 0;
+    {
+      int l1, l2, T1, T2;
+      int64_t cnt, vi, vo, S, D;
+      // in place: transform t is written only after all its A items have read
+      // it, so equal input and output strides suffice
+      l2fs_ok = lg >= 14 && l2fs_shape(d, V, l2fs_n1, &l1, &l2, &cnt, &vi, &vo) && (!inplace || vi == vo) &&
+                l2fs_ring(l1, l2, cnt, &S, &D);
+      // enough work items to fill the GPU several times over
+      if (l2fs_ok && gb_l2fs_tiles(l1, l2, &T1, &T2))
+        l2fs_busy = cnt * (((int64_t)1 << l2) / T1 + ((int64_t)1 << l1) / T2) >= 8 * 304;
+    }
+    // estimate mode takes the first candidate: the L2-resident four-step where
+    // it beat the two and three TMA passes when measured (2^14..2^21, batches
+    // that fill the GPU), then the cluster pass where it beat two TMA passes
+    // (2^14), the two passes above
+    if (!measure && l2fs_ok && l2fs_busy && lg <= 21) c.push_back("l2fs:" + std::to_string(l2fs_n1));
     if (!measure && lg >= 15 && lg <= 17 && smooth_codelet(n)) {
       const int64_t a = estimate_split(n);
       if (a > 1) c.push_back("split:" + std::to_string(a));
@@ -1645,14 +1666,7 @@ struct Builder {
       const int64_t a = estimate_split(n);
       if (a > 1) c.push_back("split:" + std::to_string(a));
     }
-    {
-      // the four-step with its intermediate in L2 (one HBM round trip)
-      int l1, l2;
-      int64_t cnt, vi, vo, S, D;
-      const int64_t n1 = lg >= 0 ? ((int64_t)1 << (lg / 2)) : 0;
-      if (lg >= 14 && measure && l2fs_shape(d, V, n1, &l1, &l2, &cnt, &vi, &vo) && l2fs_ring(l1, l2, cnt, &S, &D))
-        c.push_back("l2fs:" + std::to_string(n1));
-    }
+    if (measure && l2fs_ok) c.push_back("l2fs:" + std::to_string(l2fs_n1));
     MRChoice mc;
     if (!prec && mr_choose(d, V, false, &mc)) c.push_back("mr");
     if (smooth_codelet(n)) {

@@ -56,9 +56,9 @@ template <> __device__ __forceinline__ void codelet<4>(float2* v) { gb_dft4(v); 
 template <> __device__ __forceinline__ void codelet<8>(float2* v) { gb_dft8(v); }
 template <> __device__ __forceinline__ void codelet<16>(float2* v) { gb_dft16(v); }
 
-// the powers w^1..w^15 from (w, w^2, w^4, w^8), at most three products each
-__device__ __forceinline__ void powers16(float2* p, const float4* tw) {
-  const float4 a = __ldg(tw), b = __ldg(tw + 1);
+// the powers w^1..w^15 from (w, w^2) = a and (w^4, w^8) = b, at most three
+// products each
+__device__ __forceinline__ void powers16v(float2* p, const float4 a, const float4 b) {
   p[1] = make_float2(a.x, a.y);
   p[2] = make_float2(a.z, a.w);
   p[4] = make_float2(b.x, b.y);
@@ -71,6 +71,8 @@ __device__ __forceinline__ void powers16(float2* p, const float4* tw) {
   for (int r = 9; r < 16; ++r) p[r] = cmul(p[8], p[r - 8]);
 }
 
+__device__ __forceinline__ void powers16(float2* p, const float4* tw) { powers16v(p, __ldg(tw), __ldg(tw + 1)); }
+
 __device__ __forceinline__ void twiddle16(float2* v, const float4* tw) {
   float2 p[16];
   powers16(p, tw);
@@ -80,8 +82,9 @@ __device__ __forceinline__ void twiddle16(float2* v, const float4* tw) {
 
 // Stage S reads (+ twiddles + butterfly) for butterflies j = u + b*TPT of one
 // transform: from its padded exchange row, or (stage 0) from the landed tile
-// where element e sits at src[e * ESTRIDE].
-template <int LOGN, int S, bool FROM_TILE, int ESTRIDE>
+// where element e sits at src[e * ESTRIDE].  TWS: the stage table twt is a
+// copy in shared memory (plain loads) instead of the global one (__ldg).
+template <int LOGN, int S, bool FROM_TILE, int ESTRIDE, bool TWS = false>
 __device__ __forceinline__ void stage_in(float2* v, const float2* src, const float2* __restrict__ twt, int u,
                                          int conj) {
   using C = P2<LOGN>;
@@ -99,7 +102,15 @@ __device__ __forceinline__ void stage_in(float2* v, const float2* src, const flo
     if constexpr (L > 1) {
       static_assert(R == 16, "twiddled stages are radix 16");
       const int k = j & (L - 1);
-      twiddle16(v + b * R, reinterpret_cast<const float4*>(twt + C::twoff(S) + k * 4));
+      const float4* t4 = reinterpret_cast<const float4*>(twt + C::twoff(S) + k * 4);
+      if constexpr (TWS) {
+        float2 p[16];
+        powers16v(p, t4[0], t4[1]);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[b * R + r] = cmul(v[b * R + r], p[r]);
+      } else {
+        twiddle16(v + b * R, t4);
+      }
     }
     codelet<R>(v + b * R);
   }

@@ -99,23 +99,75 @@ __device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target) {
 
 namespace {
 
-// cp.async of 16 bytes from global (through L2 only) into shared memory
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+// an L2 policy that evicts the lines it touches first (the input and output
+// streams), so that the ring keeps its place in L2
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ void tensor_copy_4d_ef(uint32_t dst, const void* tmap, int x, int y, int z, int w,
+                                                  uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+      "%3, %4, %5}], [%6], %7;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar), "l"(policy)
+      : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// the mbarrier tracks the completion of this thread's earlier cp.async copies
-__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+// The stages after stage 0 of one n-point DFT of an item, with the stage
+// tables read from their copy in shared memory (tws); the last stage runs in
+// the store mapping.  POSTTW multiplies output k = us + q L of column col by
+// w_N^{col k} = pa s^q, where pa and s, s^2, s^4, s^8 (pb0, pb1) were loaded
+// from the post-twiddle tables at the start of the item, so that their
+// latency hides behind the stages.
+template <int LOGN, int S, bool POSTTW, int NT>
+__device__ __forceinline__ void item_stages(float2* v, float2* xrow_j, float2* xrow_s, float2* gout,
+                                            int64_t ostride, const float2* tws, int uj, int us, int conj,
+                                            float2 pa, float4 pb0, float4 pb1) {
+  using C = P2<LOGN>;
+  if constexpr (S == C::NST - 1) {
+    static_assert(C::radix(S) == 16, "the last stage is radix 16");
+    constexpr int L = C::L(S);
+    stage_in<LOGN, S, false, 1, true>(v, xrow_s, tws, us, conj);
+    float2 p[16];
+    if constexpr (POSTTW) powers16v(p, pb0, pb1);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      float2 x = v[q];
+      if constexpr (POSTTW) x = cmul(x, q == 0 ? pa : cmul(pa, p[q]));
+      if (conj) x.y = -x.y;
+      if constexpr (POSTTW) gout[(int64_t)(us + q * L) * ostride] = x;  // the ring: stays in L2
+      else __stcs(gout + (int64_t)(us + q * L) * ostride, x);            // the output stream
+    }
+  } else {
+    stage_in<LOGN, S, false, 1, true>(v, xrow_j, tws, uj, conj);
+    gb_bar<NT>();
+    stage_out_x<LOGN, S>(v, xrow_j, uj);
+    gb_bar<NT>();
+    item_stages<LOGN, S + 1, POSTTW, NT>(v, xrow_j, xrow_s, gout, ostride, tws, uj, us, conj, pa, pb0, pb1);
+  }
 }
 
 struct ItemSlot {
   long long t, j;
   int kind;  // 0 A, 1 B, -1 no more items, -2 abort
+};
+
+template <int L1, int L2>
+struct L2FSCfg {
+  static constexpr int TP = (L1 + L2 <= 16) ? 4096 : 8192;
+  static constexpr int MINB = TP == 4096 ? 2 : 1;
+  static constexpr int T1 = TP >> L1, T2 = TP >> L2;
+  static constexpr int XB = (T1 * P2<L1>::PITCH > T2 * P2<L2>::PITCH) ? T1 * P2<L1>::PITCH : T2 * P2<L2>::PITCH;
+  static_assert(XB % 2 == 0, "the stage tables after the exchange rows are 16-byte aligned");
+  static constexpr int TW = P2<L1>::twoff(P2<L1>::NST) + P2<L2>::twoff(P2<L2>::NST);
+  static constexpr size_t smem = 128 + sizeof(float2) * ((size_t)2 * TP + (size_t)XB + (size_t)TW);
 };
 
 // TP points per item (T1 = TP / n1 columns, T2 = TP / n2 rows), 16 values a
@@ -141,20 +193,25 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
   ItemSlot* info = reinterpret_cast<ItemSlot*>(smem_raw + 64);             // 2 x 24 bytes
   float2* ibuf = reinterpret_cast<float2*>(smem_raw + 128);
   float2* xbuf = ibuf + 2 * TP;
+  constexpr int XB = L2FSCfg<L1, L2>::XB;
+  float2* twa = xbuf + XB;               // stage tables of the n1-point DFTs
+  float2* twb = twa + CA::twoff(CA::NST);  // and of the n2-point DFTs
   const int tid = threadIdx.x;
   const int64_t nA = N2 / T1, nB = N1 / T2;
   const int64_t total = k.count * (nA + nB);
 
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
-      // full: one arrival per producer lane (plain, with the expected bytes, or
-      // when its cp.async copies land) plus lane 0's release of info[b]
+      // full: one arrival per producer lane (lane 0's with the expected bytes
+      // of the bulk copies) plus lane 0's release of info[b]
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(33));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 2 + b)), "r"(NT));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 4 + b)), "r"(1));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int i = tid; i < CA::twoff(CA::NST); i += blockDim.x) twa[i] = k.tw1[i];
+  for (int i = tid; i < CB::twoff(CB::NST); i += blockDim.x) twb[i] = k.tw2[i];
   __syncthreads();
   unsigned* ctr = k.sync;
   unsigned* doneA = k.sync + 1;
@@ -202,7 +259,8 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       f_a = (long long)atomicAdd(ctr, 1u);
       f_b = (long long)atomicAdd(ctr, 1u);
     }
-    bool tma0 = false, tma1 = false;  // tensor-map boxes in flight into buffer 0 / 1
+    const uint64_t pol = evict_first_policy();
+    bool tma0 = false, tma1 = false;  // bulk copies in flight into buffer 0 / 1
     uint32_t tpar0 = 0, tpar1 = 0;
     bool fail = false;
     int it = 0;
@@ -241,15 +299,24 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       }
       __syncwarp();
       float2* dst = ibuf + b * TP;
-      if (r.kind == 0 && tmap_ok) {
+      if ((r.kind == 0 && tmap_ok) || r.kind == 1) {
         if (lane == 0) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           expect_tx(full, (uint32_t)(TP * 8));
-          constexpr int BOXR = N1 < 256 ? N1 : 256;
+          if (r.kind == 0) {
+            constexpr int BOXR = N1 < 256 ? N1 : 256;
 #pragma unroll
-          for (int r0 = 0; r0 < N1; r0 += BOXR)
-            tensor_copy_4d(smem_addr(dst + r0 * T1), &tm, (int)(r.j * T1), map_coord(pos, 1, r0, (int)r.t, 0),
-                           map_coord(pos, 2, r0, (int)r.t, 0), map_coord(pos, 3, r0, (int)r.t, 0), full);
+            for (int r0 = 0; r0 < N1; r0 += BOXR)
+              tensor_copy_4d_ef(smem_addr(dst + r0 * T1), &tm, (int)(r.j * T1), map_coord(pos, 1, r0, (int)r.t, 0),
+                                map_coord(pos, 2, r0, (int)r.t, 0), map_coord(pos, 3, r0, (int)r.t, 0), full, pol);
+          } else {
+            // B: the T2 ring rows are one contiguous run of TP points; the
+            // other CTAs wrote them with ordinary stores, which the acquire
+            // above made visible to this thread, and the proxy fence to its
+            // bulk copy
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            bulk_copy(smem_addr(dst), k.ring + (r.t % k.S) * N + r.j * T2 * N2, (uint32_t)(TP * 8), full);
+          }
         } else {
           mbar_arrive(full);
         }
@@ -260,11 +327,6 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
           tma0 = true;
           tpar0 = (it >> 1) & 1;
         }
-      } else if (r.kind == 1) {
-        const float2* src = k.ring + (r.t % k.S) * N + r.j * T2 * N2;
-#pragma unroll 4
-        for (int c = lane; c < TP / 2; c += 32) cp_async16(dst + 2 * c, src + 2 * c);
-        cp_async_arrive(full);
       } else {
         mbar_arrive(full);  // an A item without tensor map (loaded by the compute warps), or the end
       }
@@ -282,7 +344,6 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       __syncwarp();
       mbar_arrive(smem_addr(bars + b));
       if (lane == 0) mbar_arrive(smem_addr(bars + b));
-      asm volatile("cp.async.wait_all;" ::: "memory");
       if (tma0) mbar_wait(smem_addr(bars + 0), tpar0);
       if (tma1) mbar_wait(smem_addr(bars + 1), tpar1);
     }
@@ -310,35 +371,31 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
     gb_bar<NT>();  // the previous item's exchange rows are read
     if (r.kind == 0) {
       // ---- A(t, j): columns [j T1, (j+1) T1) of transform t into the slot
+      const int64_t col = r.j * T1 + at;  // l2
+      const float4* pb = reinterpret_cast<const float4*>(k.ptwB + col * 4);
+      const float4 pb0 = __ldg(pb), pb1 = __ldg(pb + 1);
+      const float2 pa = __ldg(k.ptwA + col * CA::L(CA::NST - 1) + au);
       if (tmap_ok) stage_in<L1, 0, true, T1>(v, tile + at, k.tw1, au, k.conj);
       else stage_in<L1, 0, true, N2>(v, k.in + r.t * k.vis + r.j * T1 + at, k.tw1, au, k.conj);
-      const int64_t col = r.j * T1 + at;  // l2
       stage_out_x<L1, 0>(v, xbuf + at * CA::PITCH, au);
       gb_bar<NT>();
-      later_stages<L1, 1, true, false, NT>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, N2, k.tw1,
-                                           auj, au, k.conj, true, k.ptwA, k.ptwB, col);
+      item_stages<L1, 1, true, NT>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, N2, twa, auj, au,
+                                   k.conj, pa, pb0, pb1);
     } else {
       // ---- B(t, j): rows [j T2, (j+1) T2) of the slot into Y[k1 + k2 n1]
       const int64_t row0 = r.j * T2;
       stage_in<L2, 0, true, 1>(v, tile + bj * N2, k.tw2, buj, k.conj);
       stage_out_x<L2, 0>(v, xbuf + bj * CB::PITCH, buj);
       gb_bar<NT>();
-      later_stages<L2, 1, false, false, NT>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH,
-                                            k.out + r.t * k.vos + row0 + bt, N1, k.tw2, buj, bu, k.conj, true,
-                                            nullptr, nullptr, 0);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      item_stages<L2, 1, false, NT>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH,
+                                    k.out + r.t * k.vos + row0 + bt, N1, twb, buj, bu, k.conj,
+                                    make_float2(0.f, 0.f), z4, z4);
     }
     mbar_arrive(smem_addr(bars + 2 + b));  // this thread's stores are done
   }
 }
 
-template <int L1, int L2>
-struct L2FSCfg {
-  static constexpr int TP = (L1 + L2 <= 16) ? 4096 : 8192;
-  static constexpr int MINB = TP == 4096 ? 2 : 1;
-  static constexpr int T1 = TP >> L1, T2 = TP >> L2;
-  static constexpr int XB = (T1 * P2<L1>::PITCH > T2 * P2<L2>::PITCH) ? T1 * P2<L1>::PITCH : T2 * P2<L2>::PITCH;
-  static constexpr size_t smem = 128 + sizeof(float2) * ((size_t)2 * TP + (size_t)XB);
-};
 
 template <int L1, int L2>
 int grid_of() {
