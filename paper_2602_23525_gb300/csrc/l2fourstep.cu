@@ -161,13 +161,19 @@ struct ItemSlot {
 
 template <int L1, int L2>
 struct L2FSCfg {
-  static constexpr int TP = (L1 + L2 <= 16) ? 4096 : 8192;
+  // items of 4096 points (two CTAs per SM) while a column tile is at least 16
+  // columns wide; 8192 points (one CTA per SM, 8 columns and more) above,
+  // where 4096-point items measured slower (2^18..2^21)
+  static constexpr int TP = (L1 <= 8) ? 4096 : 8192;
   static constexpr int MINB = TP == 4096 ? 2 : 1;
   static constexpr int T1 = TP >> L1, T2 = TP >> L2;
   static constexpr int XB = (T1 * P2<L1>::PITCH > T2 * P2<L2>::PITCH) ? T1 * P2<L1>::PITCH : T2 * P2<L2>::PITCH;
-  static_assert(XB % 2 == 0, "the stage tables after the exchange rows are 16-byte aligned");
+  // NB item buffers, each first the landing tile of its item, then its
+  // exchange rows (a multiple of 128 bytes, the bulk copies' alignment)
+  static constexpr int NB = 3;
+  static constexpr int BUFE = (((TP > XB) ? TP : XB) + 15) / 16 * 16;
   static constexpr int TW = P2<L1>::twoff(P2<L1>::NST) + P2<L2>::twoff(P2<L2>::NST);
-  static constexpr size_t smem = 128 + sizeof(float2) * ((size_t)2 * TP + (size_t)XB + (size_t)TW);
+  static constexpr size_t smem = 256 + sizeof(float2) * ((size_t)NB * BUFE + (size_t)TW);
 };
 
 // TP points per item (T1 = TP / n1 columns, T2 = TP / n2 rows), 16 values a
@@ -175,10 +181,11 @@ struct L2FSCfg {
 // that no compute warp ever stalls on a global round trip:
 //   producer warp: takes the next item from the device counter (indices
 //     fetched two ahead), waits (bounded) until its inputs are complete,
-//     fills landing buffer b (A: tensor-map boxes; B: cp.async of the ring
-//     rows through L2) and arrives on full[b];
+//     fills item buffer b (A: tensor-map boxes of the input, evict-first in
+//     L2; B: one bulk copy of the ring rows, from L2) and arrives on full[b];
 //   compute warps: wait on full[b], compute the item's stages (named barrier
-//     1 among themselves), store, arrive on done[b];
+//     1 among themselves) with buffer b as the exchange rows once the tile is
+//     read, store, arrive on done[b];
 //   publisher warp: after done[b], hands buffer b back (pub[b]) and publishes
 //     the item to the other CTAs (a gpu-scope fence, then the count).
 template <int L1, int L2, int TP, int MINB>
@@ -189,24 +196,23 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
   constexpr int N1 = CA::N, N2 = CB::N, T1 = TP / N1, T2 = TP / N2, NT = TP / 16;
   constexpr int64_t N = (int64_t)N1 * N2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                  // full[2], done[2], pub[2]
-  ItemSlot* info = reinterpret_cast<ItemSlot*>(smem_raw + 64);             // 2 x 24 bytes
-  float2* ibuf = reinterpret_cast<float2*>(smem_raw + 128);
-  float2* xbuf = ibuf + 2 * TP;
-  constexpr int XB = L2FSCfg<L1, L2>::XB;
-  float2* twa = xbuf + XB;               // stage tables of the n1-point DFTs
+  constexpr int NB = L2FSCfg<L1, L2>::NB, BUFE = L2FSCfg<L1, L2>::BUFE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                  // full[NB], done[NB], pub[NB]
+  ItemSlot* info = reinterpret_cast<ItemSlot*>(smem_raw + 128);            // NB x 24 bytes
+  float2* ibuf = reinterpret_cast<float2*>(smem_raw + 256);                // NB item buffers
+  float2* twa = ibuf + NB * BUFE;        // stage tables of the n1-point DFTs
   float2* twb = twa + CA::twoff(CA::NST);  // and of the n2-point DFTs
   const int tid = threadIdx.x;
   const int64_t nA = N2 / T1, nB = N1 / T2;
   const int64_t total = k.count * (nA + nB);
 
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       // full: one arrival per producer lane (lane 0's with the expected bytes
       // of the bulk copies) plus lane 0's release of info[b]
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(33));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 2 + b)), "r"(NT));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 4 + b)), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + NB + b)), "r"(NT));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 2 * NB + b)), "r"(1));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -224,21 +230,19 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
     // CTAs: a gpu-scope fence (the compute warps' stores, ordered before
     // their arrival on done[b], become visible first), then the count.
     const int lane = tid - NT - 32;
-    for (int it = 0;; ++it) {
-      const int b = it & 1;
-      const uint32_t par = (it >> 1) & 1;
+    for (int b = 0, par = 0;; b = (b + 1 == NB) ? 0 : b + 1, par ^= (b == 0)) {
       if (!mbar_wait(smem_addr(bars + b), par)) {
         if (lane == 0) gb_set_status(k.status, kStatusTimeout);
         break;
       }
       const ItemSlot r = info[b];
       if (r.kind < 0) break;
-      if (!mbar_wait(smem_addr(bars + 2 + b), par)) {
+      if (!mbar_wait(smem_addr(bars + NB + b), par)) {
         if (lane == 0) gb_set_status(k.status, kStatusTimeout);
         break;
       }
       if (lane == 0) {
-        mbar_arrive(smem_addr(bars + 4 + b));
+        mbar_arrive(smem_addr(bars + 2 * NB + b));
         __threadfence();
         atomicAdd((r.kind == 0 ? doneA : doneB) + r.t, 1u);
       }
@@ -260,20 +264,18 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       f_b = (long long)atomicAdd(ctr, 1u);
     }
     const uint64_t pol = evict_first_policy();
-    bool tma0 = false, tma1 = false;  // bulk copies in flight into buffer 0 / 1
-    uint32_t tpar0 = 0, tpar1 = 0;
+    unsigned tma = 0, tpar = 0;  // bit b: bulk copies in flight into buffer b, and their phase
     bool fail = false;
-    int it = 0;
-    for (;; ++it) {
-      const int b = it & 1;
+    int it = 0, b = 0;
+    uint32_t ph = 0;  // phase of the buffers in this round of NB items
+    for (;; ++it, b = (b + 1 == NB) ? 0 : b + 1, ph ^= (b == 0)) {
       const uint32_t full = smem_addr(bars + b);
-      if (it >= 2) {
-        if (!mbar_wait(smem_addr(bars + 4 + b), ((it - 2) >> 1) & 1)) {
+      if (it >= NB) {
+        if (!mbar_wait(smem_addr(bars + 2 * NB + b), ph ^ 1)) {
           fail = true;
           break;
         }
-        if (b) tma1 = false;
-        else tma0 = false;
+        tma &= ~(1u << b);
       }
       long long idx = 0;
       if (lane == 0) {
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
         break;
       }
       __syncwarp();
-      float2* dst = ibuf + b * TP;
+      float2* dst = ibuf + b * BUFE;
       if ((r.kind == 0 && tmap_ok) || r.kind == 1) {
         if (lane == 0) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -320,13 +322,8 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
         } else {
           mbar_arrive(full);
         }
-        if (b) {
-          tma1 = true;
-          tpar1 = (it >> 1) & 1;
-        } else {
-          tma0 = true;
-          tpar0 = (it >> 1) & 1;
-        }
+        tma |= 1u << b;
+        tpar = (tpar & ~(1u << b)) | (ph << b);
       } else {
         mbar_arrive(full);  // an A item without tensor map (loaded by the compute warps), or the end
       }
@@ -335,8 +332,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
     }
     if (fail) {
       // a wait gave up: stop the compute and publisher warps at the item they
-      // wait for next (buffer it & 1, not armed), then let copies in flight land
-      const int b = it & 1;
+      // wait for next (buffer b, not armed), then let copies in flight land
       if (lane == 0) {
         gb_set_status(k.status, kStatusTimeout);
         info[b] = ItemSlot{0, 0, -2};
@@ -344,8 +340,8 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       __syncwarp();
       mbar_arrive(smem_addr(bars + b));
       if (lane == 0) mbar_arrive(smem_addr(bars + b));
-      if (tma0) mbar_wait(smem_addr(bars + 0), tpar0);
-      if (tma1) mbar_wait(smem_addr(bars + 1), tpar1);
+      for (int q = 0; q < NB; ++q)
+        if ((tma >> q) & 1) mbar_wait(smem_addr(bars + q), (tpar >> q) & 1);
     }
     return;
   }
@@ -358,17 +354,16 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
   const int bj = tid / CB::TPT, buj = tid % CB::TPT;
   const int bt = tid % T2, bu = tid / T2;
   float2 v[16];
-  for (int it = 0;; ++it) {
-    const int b = it & 1;
-    if (!mbar_wait(smem_addr(bars + b), (it >> 1) & 1)) {
+  for (int b = 0, ph = 0;; b = (b + 1 == NB) ? 0 : b + 1, ph ^= (b == 0)) {
+    if (!mbar_wait(smem_addr(bars + b), ph)) {
       if (tid == 0) gb_set_status(k.status, kStatusTimeout);
       break;
     }
     const ItemSlot r = info[b];
     if (r.kind < 0) break;
-    const float2* tile = ibuf + b * TP;
+    float2* xbuf = ibuf + b * BUFE;  // the item's tile, then its exchange rows
+    const float2* tile = xbuf;
     float2* slot = k.ring + (r.t % k.S) * N;
-    gb_bar<NT>();  // the previous item's exchange rows are read
     if (r.kind == 0) {
       // ---- A(t, j): columns [j T1, (j+1) T1) of transform t into the slot
       const int64_t col = r.j * T1 + at;  // l2
@@ -377,6 +372,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       const float2 pa = __ldg(k.ptwA + col * CA::L(CA::NST - 1) + au);
       if (tmap_ok) stage_in<L1, 0, true, T1>(v, tile + at, k.tw1, au, k.conj);
       else stage_in<L1, 0, true, N2>(v, k.in + r.t * k.vis + r.j * T1 + at, k.tw1, au, k.conj);
+      gb_bar<NT>();  // the tile is read: its buffer takes the exchange rows
       stage_out_x<L1, 0>(v, xbuf + at * CA::PITCH, au);
       gb_bar<NT>();
       item_stages<L1, 1, true, NT>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, N2, twa, auj, au,
@@ -385,6 +381,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       // ---- B(t, j): rows [j T2, (j+1) T2) of the slot into Y[k1 + k2 n1]
       const int64_t row0 = r.j * T2;
       stage_in<L2, 0, true, 1>(v, tile + bj * N2, k.tw2, buj, k.conj);
+      gb_bar<NT>();  // the tile is read: its buffer takes the exchange rows
       stage_out_x<L2, 0>(v, xbuf + bj * CB::PITCH, buj);
       gb_bar<NT>();
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -392,7 +389,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
                                     k.out + r.t * k.vos + row0 + bt, N1, twb, buj, bu, k.conj,
                                     make_float2(0.f, 0.f), z4, z4);
     }
-    mbar_arrive(smem_addr(bars + 2 + b));  // this thread's stores are done
+    mbar_arrive(smem_addr(bars + NB + b));  // this thread's stores are done
   }
 }
 
