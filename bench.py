@@ -49,19 +49,30 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# kernel family -> (committed ncu traffic record, the sources its hash covers)
+TRAFFIC_RECORDS = {
+    "p2-tma": ("p2_tma_traffic.txt",
+               ("stockham_pow2.cu", "gb_p2_stages.cuh", "gb_tma.cuh", "gb_kernels.h", "codelets.cuh")),
+    "l2-fourstep": ("l2fs_traffic.txt",
+                    ("l2fourstep.cu", "gb_p2_stages.cuh", "gb_tma.cuh", "gb_kernels.h", "codelets.cuh")),
+}
+
+
+def kernel_source_hash(family="p2-tma"):
     h = hashlib.sha256()
-    for name in ("stockham_pow2.cu", "gb_p2_stages.cuh", "gb_tma.cuh", "gb_kernels.h", "codelets.cuh"):
+    for name in TRAFFIC_RECORDS[family][1]:
         with open(os.path.join(ROOT, "paper_2602_23525_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary
+def recorded_traffic(family="p2-tma"):
+    """DRAM bytes per launch of a kernel family from its committed ncu summary
     (``key: value`` lines), valid only if the kernel sources are unchanged since
     the capture."""
-    path = os.path.join(ROOT, "profiles", "p2_tma_traffic.txt")
+    if family not in TRAFFIC_RECORDS:
+        return None
+    path = os.path.join(ROOT, "profiles", TRAFFIC_RECORDS[family][0])
     if not os.path.exists(path):
         return None
     d = {}
@@ -70,7 +81,7 @@ def recorded_traffic():
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 d[k.strip()] = v.strip()
-    if d.get("kernel_hash") != kernel_source_hash():
+    if d.get("kernel_hash") != kernel_source_hash(family):
         return None
     try:
         d["dram_bytes_per_launch"] = float(d["dram_bytes_per_launch"])
@@ -255,7 +266,7 @@ def run_gpu(args, rank, world):
     # the scratch round trips of multi-pass plans are not algorithmic
     achieved = fam_alg[dom] / (fam_ms[dom] * 1e-3) / 1e9
     pass_achieved = fam_pass[dom] / (fam_ms[dom] * 1e-3) / 1e9
-    traffic = recorded_traffic()
+    traffic = recorded_traffic(dom)
     traffic_exec = None
     if traffic:
         # DRAM bytes of one execution of the family's average plan: its launches
@@ -265,6 +276,7 @@ def run_gpu(args, rank, world):
         traffic_exec = sum(nl * per_pt * pts for nl, pts in runs) / len(runs)
         alg_exec = sum(16.0 * pts for _, pts in runs) / len(runs)
     kernel_names = {"p2-tma": "gb_p2_kernel / gb_p2small_kernel (TMA power-of-two passes)",
+                    "l2-fourstep": "gb_l2fs_kernel (the four-step in one persistent kernel, intermediate in L2)",
                     "cluster": "gb_cluster_kernel (one pass over a thread-block cluster)",
                     "stockham": "gb_stockham_kernel (generic pass)"}
 
@@ -400,9 +412,11 @@ def time_oracle(sample):
     return flops, dt, threads
 
 
-def cpu_baseline(budget_s=20.0):
-    # eight times the base sample: about 10-15 s of oracle work on 16 host cores
-    sample = cpu_sample(8.0)
+def cpu_baseline(target_s=12.0):
+    # the base sample once to size the run, then the base sample scaled so that
+    # the timed oracle work takes about target_s seconds on the host's cores
+    _, t1, _ = time_oracle(cpu_sample(1.0))
+    sample = cpu_sample(min(32.0, max(1.0, target_s / max(t1, 1e-3))))
     flops, dt, threads = time_oracle(sample)
     desc = ", ".join(f"{c} x n={n}" for n, c in sample)
     return {"value": round(flops / dt / 1e9, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
@@ -780,7 +794,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-lanes", type=int, default=2, help="e2e: streams the problems rotate over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of timed oracle work")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
