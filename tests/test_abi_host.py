@@ -234,6 +234,21 @@ def test_cluster_plans_and_wisdom():
     gbfft.fft_forget_wisdom()
 
 
+def test_plan_l2_resident_four_step():
+    """Estimate mode takes the four-step in one persistent kernel with its
+    intermediate in an L2 ring (eq. (2), one HBM round trip) for contiguous
+    2^14..2^21 batches that fill the GPU several times over, split n1 = 2^floor(e/2);
+    small batches, 2^22 and strided layouts keep the cluster or TMA passes."""
+    for e in range(14, 22):
+        n = 2 ** e
+        txt = explain([(n, 1, 1)], [(2 ** 26 // n, n, n)])
+        assert f"pass l2-fourstep n={n} = {2 ** (e // 2)} x {n >> (e // 2)}" in txt, txt
+        assert txt.count("pass ") == 1, txt
+    assert "l2-fourstep" not in explain([(2 ** 22, 1, 1)], [(16, 2 ** 22, 2 ** 22)])
+    assert "l2-fourstep" not in explain([(65536, 1, 1)], [(8, 65536, 65536)])
+    assert "l2-fourstep" not in explain([(65536, 1024, 1024)], [(1024, 1, 1)])
+
+
 def test_plan_layout_specific_four_steps():
     """The four-step (eq. (2)) picks its scratch layout from the problem's
     strides: columns innermost for transforms down the columns of a row-major
