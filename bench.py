@@ -413,8 +413,10 @@ def time_oracle(sample):
 
 
 def cpu_baseline(target_s=12.0):
-    # the base sample once to size the run, then the base sample scaled so that
-    # the timed oracle work takes about target_s seconds on the host's cores
+    # the base sample twice (the first run loads the oracle and its threads) to
+    # size the run, then the base sample scaled so that the timed oracle work
+    # takes about target_s seconds on the host's cores
+    time_oracle(cpu_sample(1.0))
     _, t1, _ = time_oracle(cpu_sample(1.0))
     sample = cpu_sample(min(32.0, max(1.0, target_s / max(t1, 1e-3))))
     flops, dt, threads = time_oracle(sample)
