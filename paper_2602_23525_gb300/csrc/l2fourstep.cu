@@ -157,6 +157,7 @@ __device__ __forceinline__ void item_stages(float2* v, float2* xrow_j, float2* x
 struct ItemSlot {
   long long t, j;
   int kind;  // 0 A, 1 B, -1 no more items, -2 abort
+  int slot;  // t mod S, formed once by the producer (a 64-bit remainder)
 };
 
 template <int L1, int L2>
@@ -188,7 +189,9 @@ struct L2FSCfg {
 //     read, store, arrive on done[b];
 //   publisher warp: after done[b], hands buffer b back (pub[b]) and publishes
 //     the item to the other CTAs (a gpu-scope fence, then the count).
-template <int L1, int L2, int TP, int MINB>
+// CONJ: the backward transform (inputs and outputs conjugated), a template
+// argument so that the forward kernel carries no conjugation code
+template <int L1, int L2, int TP, int MINB, int CONJ>
 __global__ void __launch_bounds__(TP / 16 + 64, MINB)
     gb_l2fs_kernel(const __grid_constant__ GbL2FS k, const __grid_constant__ CUtensorMap tm, int tmap_ok, int pos) {
   using CA = P2<L1>;
@@ -284,10 +287,10 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
         f_b = (long long)atomicAdd(ctr, 1u);  // used two items from now
       }
       idx = __shfl_sync(0xffffffffu, idx, 0);
-      ItemSlot r{0, 0, -1};
+      ItemSlot r{0, 0, -1, 0};
       if (idx < total) {
         const ItemRef d = decode(idx, k.count, k.D, nA, nB);
-        r = ItemSlot{d.t, d.j, d.kind};
+        r = ItemSlot{d.t, d.j, d.kind, (int)(d.t % k.S)};
       }
       int ok = 1;
       if (lane == 0) {
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
             // above made visible to this thread, and the proxy fence to its
             // bulk copy
             asm volatile("fence.proxy.async.global;" ::: "memory");
-            bulk_copy(smem_addr(dst), k.ring + (r.t % k.S) * N + r.j * T2 * N2, (uint32_t)(TP * 8), full);
+            bulk_copy(smem_addr(dst), k.ring + (int64_t)r.slot * N + r.j * T2 * N2, (uint32_t)(TP * 8), full);
           }
         } else {
           mbar_arrive(full);
@@ -335,7 +338,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       // wait for next (buffer b, not armed), then let copies in flight land
       if (lane == 0) {
         gb_set_status(k.status, kStatusTimeout);
-        info[b] = ItemSlot{0, 0, -2};
+        info[b] = ItemSlot{0, 0, -2, 0};
       }
       __syncwarp();
       mbar_arrive(smem_addr(bars + b));
@@ -363,30 +366,30 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
     if (r.kind < 0) break;
     float2* xbuf = ibuf + b * BUFE;  // the item's tile, then its exchange rows
     const float2* tile = xbuf;
-    float2* slot = k.ring + (r.t % k.S) * N;
+    float2* slot = k.ring + (int64_t)r.slot * N;
     if (r.kind == 0) {
       // ---- A(t, j): columns [j T1, (j+1) T1) of transform t into the slot
       const int64_t col = r.j * T1 + at;  // l2
       const float4* pb = reinterpret_cast<const float4*>(k.ptwB + col * 4);
       const float4 pb0 = __ldg(pb), pb1 = __ldg(pb + 1);
       const float2 pa = __ldg(k.ptwA + col * CA::L(CA::NST - 1) + au);
-      if (tmap_ok) stage_in<L1, 0, true, T1>(v, tile + at, k.tw1, au, k.conj);
-      else stage_in<L1, 0, true, N2>(v, k.in + r.t * k.vis + r.j * T1 + at, k.tw1, au, k.conj);
+      if (tmap_ok) stage_in<L1, 0, true, T1>(v, tile + at, k.tw1, au, CONJ);
+      else stage_in<L1, 0, true, N2>(v, k.in + r.t * k.vis + r.j * T1 + at, k.tw1, au, CONJ);
       gb_bar<NT>();  // the tile is read: its buffer takes the exchange rows
       stage_out_x<L1, 0>(v, xbuf + at * CA::PITCH, au);
       gb_bar<NT>();
       item_stages<L1, 1, true, NT>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, N2, twa, auj, au,
-                                   k.conj, pa, pb0, pb1);
+                                   CONJ, pa, pb0, pb1);
     } else {
       // ---- B(t, j): rows [j T2, (j+1) T2) of the slot into Y[k1 + k2 n1]
       const int64_t row0 = r.j * T2;
-      stage_in<L2, 0, true, 1>(v, tile + bj * N2, k.tw2, buj, k.conj);
+      stage_in<L2, 0, true, 1>(v, tile + bj * N2, k.tw2, buj, CONJ);
       gb_bar<NT>();  // the tile is read: its buffer takes the exchange rows
       stage_out_x<L2, 0>(v, xbuf + bj * CB::PITCH, buj);
       gb_bar<NT>();
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
       item_stages<L2, 1, false, NT>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH,
-                                    k.out + r.t * k.vos + row0 + bt, N1, twb, buj, bu, k.conj,
+                                    k.out + r.t * k.vos + row0 + bt, N1, twb, buj, bu, CONJ,
                                     make_float2(0.f, 0.f), z4, z4);
     }
     mbar_arrive(smem_addr(bars + NB + b));  // this thread's stores are done
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
 template <int L1, int L2>
 int grid_of() {
   using G = L2FSCfg<L1, L2>;
-  auto fn = gb_l2fs_kernel<L1, L2, G::TP, G::MINB>;
+  auto fn = gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 0>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -436,7 +439,15 @@ cudaError_t launch(const GbL2FS& k, cudaStream_t st) {
   memset(&tm, 0, sizeof(tm));
   int pos = 0;
   const int tmap_ok = gb_p2_rows_map(g, G::T1, &tm, &pos);
-  gb_l2fs_kernel<L1, L2, G::TP, G::MINB><<<(unsigned)grid, G::TP / 16 + 64, G::smem, st>>>(k, tm, tmap_ok, pos);
+  if (k.conj) {
+    auto fb = gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 1>;
+    if (cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem) != cudaSuccess)
+      return cudaGetLastError();
+    fb<<<(unsigned)grid, G::TP / 16 + 64, G::smem, st>>>(k, tm, tmap_ok, pos);
+  } else {
+    gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 0><<<(unsigned)grid, G::TP / 16 + 64, G::smem, st>>>(k, tm, tmap_ok,
+                                                                                            pos);
+  }
   return cudaGetLastError();
 }
 
