@@ -1128,9 +1128,10 @@ struct Builder {
   // in an L2-resident ring (l2fourstep.cu): contiguous power-of-two transforms
   // of 2^14 .. 2^22 points, at most one vector loop.  The lag D between the A
   // and B items of a transform is kL2Lag items per CTA of the persistent grid
-  // (a CTA holds up to five items at once: two claimed, three in its buffers;
+  // (a CTA holds up to four items at once: one claimed, three in its buffers;
   // with a lag of two the B items waited on their A items for a fifth of the
-  // time, measured); the ring holds S = 2D transforms within kL2RingBytes
+  // time, and lags of eight, with rings up to 96 MiB, were slower again than
+  // five: measured); the ring holds S = 2D transforms within kL2RingBytes
   // (S > D is required).
   static constexpr int64_t kL2RingBytes = (int64_t)64 << 20;
   static constexpr int64_t kL2Lag = 5;

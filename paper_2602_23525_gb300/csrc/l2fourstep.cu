@@ -181,7 +181,7 @@ struct L2FSCfg {
 // compute thread, NT = TP / 16 compute threads plus two control warps, so
 // that no compute warp ever stalls on a global round trip:
 //   producer warp: takes the next item from the device counter (indices
-//     fetched two ahead), waits (bounded) until its inputs are complete,
+//     fetched one ahead), waits (bounded) until its inputs are complete,
 //     fills item buffer b (A: tensor-map boxes of the input, evict-first in
 //     L2; B: one bulk copy of the ring rows, from L2) and arrives on full[b];
 //   compute warps: wait on full[b], compute the item's stages (named barrier
@@ -256,16 +256,13 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
 
   if (tid >= NT) {
     // ---------------------------------------------------------------- producer warp
-    // takes the next item (indices fetched two ahead), waits (bounded) until
+    // takes the next item (indices fetched one ahead), waits (bounded) until
     // its inputs are complete -- B: the A items of its transform; A: the B
     // items of the transform whose slot it rewrites -- and fills landing
     // buffer b once the publisher has handed it back.
     const int lane = tid - NT;
-    long long f_a = 0, f_b = 0;
-    if (lane == 0) {
-      f_a = (long long)atomicAdd(ctr, 1u);
-      f_b = (long long)atomicAdd(ctr, 1u);
-    }
+    long long f_a = 0;
+    if (lane == 0) f_a = (long long)atomicAdd(ctr, 1u);
     const uint64_t pol = evict_first_policy();
     unsigned tma = 0, tpar = 0;  // bit b: bulk copies in flight into buffer b, and their phase
     bool fail = false;
@@ -282,9 +279,10 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       }
       long long idx = 0;
       if (lane == 0) {
+        // one claim ahead hides the atomic's round trip; two held items
+        // longer before they started and measured slower
         idx = f_a;
-        f_a = f_b;
-        f_b = (long long)atomicAdd(ctr, 1u);  // used two items from now
+        f_a = (long long)atomicAdd(ctr, 1u);
       }
       idx = __shfl_sync(0xffffffffu, idx, 0);
       ItemSlot r{0, 0, -1, 0};
