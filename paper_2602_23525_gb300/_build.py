@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["stockham.cu", "group_kernel.cu", "stockham_pow2.cu", "tc.cu", "tables.cu", "bluestein.cu", "rader.cu", "real.cu", "plan.cpp", "builder.cpp", "api.cpp", "group.cpp", "server.cpp", "noalloc.cu", "cluster.cu", "l2fourstep.cu", "stockham_mr.cu", "stockham_mr512.cu"]
+SOURCES = ["stockham.cu", "group_kernel.cu", "stockham_pow2.cu", "tc.cu", "tables.cu", "bluestein.cu", "rader.cu", "real.cu", "plan.cpp", "builder.cpp", "api.cpp", "group.cpp", "server.cpp", "noalloc.cu", "cluster.cu", "l2fourstep.cu", "stockham_mr.cu", "stockham_mr512.cu", "stockham_mrc.cu", "stockham_mrc2.cu"]
 
 
 def nvcc() -> str:

@@ -33,6 +33,7 @@
 #include <stdint.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "codelets.cuh"
 #include "gb_kernels.h"
@@ -274,8 +275,64 @@ __device__ __forceinline__ void any_stage(int R, float2* v, const Src& src, floa
   }
 }
 
-// NT threads per CTA; TMA: 0 plain loads, 1 copy engine
-template <int NT, int LOAD, int STORE, bool POSTTW>
+// A radix schedule fixed at compile time (radices 2..16 of the codelets):
+// every stage's radix, L, butterfly count and divisor are constants, so each
+// stage is straight-line code for its radix -- no switch over radices, no
+// run-time division by L.  Threads per transform as gb_mr_threads.
+template <int... RS>
+struct MRS {
+  static constexpr int NST = sizeof...(RS);
+  static constexpr int N = (RS * ...);
+  __host__ __device__ static constexpr int radix(int s) {
+    constexpr int r[] = {RS...};
+    return r[s];
+  }
+  __host__ __device__ static constexpr int L(int s) {
+    int l = 1;
+    for (int i = 0; i < s; ++i) l *= radix(i);
+    return l;
+  }
+  __host__ __device__ static constexpr int tpt() {
+    int t = 1;
+    for (int s = 0; s < NST; ++s) {
+      const int R = radix(s), need = (N / R + 16 / R - 1) / (16 / R);
+      if (need > t) t = need;
+    }
+    return t;
+  }
+  static bool matches(const GbMR& k) {
+    if (k.n != N || k.nst != NST || k.tpt != tpt()) return false;
+    for (int s = 0; s < NST; ++s)
+      if (k.radix[s] != radix(s)) return false;
+    return true;
+  }
+};
+
+// stages S.. of a compile-time schedule from the exchange rows, the last one
+// to global memory
+template <class SCH, int S>
+__device__ __forceinline__ void static_stages(float2* v, float2* xbuf, const Dst& dst, const GbMR& k, int tj, int uj,
+                                              bool vj, int ts, int us, bool vs, int64_t cnt) {
+  if constexpr (S < SCH::NST) {
+    constexpr bool last = S == SCH::NST - 1;
+    constexpr int R = SCH::radix(S), L = SCH::L(S);
+    constexpr unsigned LM = (unsigned)((1ull << 32) / (unsigned long long)L);
+    const int t = last ? ts : tj, u = last ? us : uj;
+    const bool ok = (last ? vs : vj) && t < cnt;
+    Src sx;
+    sx.p = xbuf + t * k.pitch;
+    sx.stride = 1;
+    sx.padded = true;
+    sx.conj = false;
+    run_stage<R>(v, sx, xbuf + t * k.pitch, last ? &dst : nullptr, u, SCH::tpt(), SCH::N, L, LM, k.tw[S], ok, true);
+    __syncthreads();
+    static_stages<SCH, S + 1>(v, xbuf, dst, k, tj, uj, vj, ts, us, vs, cnt);
+  }
+}
+
+// NT threads per CTA; TMA: 0 plain loads, 1 copy engine; SCH: a compile-time
+// radix schedule (MRS) or void (the schedule in k, read at run time)
+template <int NT, int LOAD, int STORE, bool POSTTW, class SCH = void>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     gb_mr_kernel(const __grid_constant__ GbMR k, const __grid_constant__ CUtensorMap tm, int tma) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -286,8 +343,14 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
   const int TL = (k.T * k.land + 15) & ~15;
   float2* xbuf = land + 2 * TL;
 
+  constexpr bool kStatic = !std::is_void_v<SCH>;
   const int tid = threadIdx.x;
-  const int T = k.T, tpt = k.tpt, n = k.n;
+  const int T = k.T;
+  int tpt = k.tpt, n = k.n;
+  if constexpr (kStatic) {
+    tpt = SCH::tpt();
+    n = SCH::N;
+  }
   const int tj = tid / tpt, uj = tid - tj * tpt;  // lanes along a transform
   const int tt = tid % T, ut = tid / T;           // lanes across the transforms
   const bool vj = tj < T, vt = ut < tpt;
@@ -398,7 +461,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     const bool last0 = k.nst == 1;
     const bool ok0 = v0 && t0 < cnt;
     // one stage: the host builds this only when the load and store mappings agree
-    if (k.radix[0] > 16)
+    if constexpr (kStatic)
+      run_stage<SCH::radix(0)>(v, s0, xbuf + t0 * k.pitch, SCH::NST == 1 ? &dst : nullptr, u0, tpt, n, 1, 0, nullptr,
+                               ok0, true);
+    else if (k.radix[0] > 16)
       generic_stage(s0, xbuf + t0 * k.pitch, last0 ? &dst : nullptr, u0, tpt, n, k.radix[0], k.wp, ok0);
     else
       any_stage(k.radix[0], v, s0, xbuf + t0 * k.pitch, last0 ? &dst : nullptr, u0, tpt, n, k.L[0], k.Lmagic[0],
@@ -412,25 +478,29 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
       }
     }
     __syncthreads();
-    for (int s = 1; s < k.nst; ++s) {
-      const bool last = s == k.nst - 1;
-      const int t = last ? ts : tj, u = last ? us : uj;
-      const bool ok = (last ? vs : vj) && t < cnt;
-      Src sx;
-      sx.p = xbuf + t * k.pitch;
-      sx.stride = 1;
-      sx.padded = true;
-      sx.conj = false;
-      any_stage(k.radix[s], v, sx, xbuf + t * k.pitch, last ? &dst : nullptr, u, tpt, n, k.L[s], k.Lmagic[s],
-                k.tw[s], ok, true);
-      __syncthreads();
+    if constexpr (kStatic) {
+      static_stages<SCH, 1>(v, xbuf, dst, k, tj, uj, vj, ts, us, vs, cnt);
+    } else {
+      for (int s = 1; s < k.nst; ++s) {
+        const bool last = s == k.nst - 1;
+        const int t = last ? ts : tj, u = last ? us : uj;
+        const bool ok = (last ? vs : vj) && t < cnt;
+        Src sx;
+        sx.p = xbuf + t * k.pitch;
+        sx.stride = 1;
+        sx.padded = true;
+        sx.conj = false;
+        any_stage(k.radix[s], v, sx, xbuf + t * k.pitch, last ? &dst : nullptr, u, tpt, n, k.L[s], k.Lmagic[s],
+                  k.tw[s], ok, true);
+        __syncthreads();
+      }
     }
   }
 }
 
-template <int NT, int LOAD, int STORE, bool POSTTW>
+template <int NT, int LOAD, int STORE, bool POSTTW, class SCH = void>
 cudaError_t launch(const GbMR& k, cudaStream_t st) {
-  auto fn = gb_mr_kernel<NT, LOAD, STORE, POSTTW>;
+  auto fn = gb_mr_kernel<NT, LOAD, STORE, POSTTW, SCH>;
   const size_t smem = gb_mr_smem(k);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -476,17 +546,17 @@ cudaError_t launch(const GbMR& k, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int NT>
+template <int NT, class SCH = void>
 cudaError_t dispatch(const GbMR& k, cudaStream_t st) {
   if (k.load == GB_P2_LOAD_CONTIG && k.store == GB_P2_STORE_CONTIG && !k.posttw)
-    return launch<NT, GB_P2_LOAD_CONTIG, GB_P2_STORE_CONTIG, false>(k, st);
+    return launch<NT, GB_P2_LOAD_CONTIG, GB_P2_STORE_CONTIG, false, SCH>(k, st);
   if (k.load == GB_P2_LOAD_CONTIG && k.store == GB_P2_STORE_COLS && !k.posttw)
-    return launch<NT, GB_P2_LOAD_CONTIG, GB_P2_STORE_COLS, false>(k, st);
+    return launch<NT, GB_P2_LOAD_CONTIG, GB_P2_STORE_COLS, false, SCH>(k, st);
   if (k.load == GB_P2_LOAD_ROWS && k.store == GB_P2_STORE_CONTIG && !k.posttw)
-    return launch<NT, GB_P2_LOAD_ROWS, GB_P2_STORE_CONTIG, false>(k, st);
+    return launch<NT, GB_P2_LOAD_ROWS, GB_P2_STORE_CONTIG, false, SCH>(k, st);
   if (k.load == GB_P2_LOAD_ROWS && k.store == GB_P2_STORE_COLS)
-    return k.posttw ? launch<NT, GB_P2_LOAD_ROWS, GB_P2_STORE_COLS, true>(k, st)
-                    : launch<NT, GB_P2_LOAD_ROWS, GB_P2_STORE_COLS, false>(k, st);
+    return k.posttw ? launch<NT, GB_P2_LOAD_ROWS, GB_P2_STORE_COLS, true, SCH>(k, st)
+                    : launch<NT, GB_P2_LOAD_ROWS, GB_P2_STORE_COLS, false, SCH>(k, st);
   return cudaErrorInvalidValue;
 }
 
@@ -495,3 +565,6 @@ cudaError_t dispatch(const GbMR& k, cudaStream_t st) {
 // the kernel launch for CTAs of 256 / 512 threads (one translation unit each)
 cudaError_t gb_mr_dispatch_256(const GbMR& k, cudaStream_t st);
 cudaError_t gb_mr_dispatch_512(const GbMR& k, cudaStream_t st);
+// the compile-time schedules (stockham_mrc.cu): returns 1 and sets *e when
+// k's length and schedule are one of them, else 0
+int gb_mr_dispatch_static(const GbMR& k, cudaStream_t st, cudaError_t* e);

@@ -47,6 +47,8 @@ size_t gb_mr_smem(const GbMR& k) {
 cudaError_t gb_mr_dispatch_256(const GbMR& k, cudaStream_t st) { return dispatch<256>(k, st); }
 
 cudaError_t gb_launch_mr(const GbMR& k, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (gb_mr_dispatch_static(k, st, &e)) return e;
   if (k.T * k.tpt <= 256) return gb_mr_dispatch_256(k, st);
   if (k.T * k.tpt <= 512) return gb_mr_dispatch_512(k, st);
   return cudaErrorInvalidValue;
