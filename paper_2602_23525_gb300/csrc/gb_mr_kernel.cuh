@@ -333,7 +333,7 @@ __device__ __forceinline__ void static_stages(float2* v, float2* xbuf, const Dst
 // NT threads per CTA; TMA: 0 plain loads, 1 copy engine; SCH: a compile-time
 // radix schedule (MRS) or void (the schedule in k, read at run time)
 template <int NT, int LOAD, int STORE, bool POSTTW, class SCH = void>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(NT, NT <= 256 ? (std::is_void_v<SCH> ? 2 : 3) : 1)
     gb_mr_kernel(const __grid_constant__ GbMR k, const __grid_constant__ CUtensorMap tm, int tma) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
