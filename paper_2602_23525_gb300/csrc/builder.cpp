@@ -176,8 +176,10 @@ struct Builder {
     const int lg = log2_exact(n);
     if (lg >= 12) {
       // powers of two: a near-square split, so that both passes are one-CTA
-      // TMA passes up to 2^20; three passes beyond
-      const int e1 = lg <= 20 ? lg / 2 : (lg + 2) / 3;
+      // TMA passes up to 2^20; 2^22..2^24 as n1 x 65536, whose 65536-point
+      // transforms the L2-resident four-step takes in groups; three passes
+      // otherwise
+      const int e1 = lg <= 20 ? lg / 2 : (lg >= 22 && lg <= 24) ? lg - 16 : (lg + 2) / 3;
       return (int64_t)1 << e1;
     }
     int64_t best = 0;
@@ -1126,7 +1128,8 @@ struct Builder {
 
   // The four-step of eq. (2) as one persistent kernel whose intermediate stays
   // in an L2-resident ring (l2fourstep.cu): contiguous power-of-two transforms
-  // of 2^14 .. 2^22 points, at most one vector loop.  The lag D between the A
+  // of 2^14 .. 2^22 points, at most one vector loop, and (group mode) the
+  // 65536-point inner transforms of 2^22..2^24-point four-steps.  The lag D between the A
   // and B items of a transform is kL2Lag items per CTA of the persistent grid
   // (a CTA holds up to four items at once: one claimed, three in its buffers;
   // with a lag of two the B items waited on their A items for a fifth of the
@@ -1136,46 +1139,87 @@ struct Builder {
   static constexpr int64_t kL2RingBytes = (int64_t)64 << 20;
   static constexpr int64_t kL2Lag = 5;
 
-  bool l2fs_shape(const Dim& d, const std::vector<Dim>& V, int64_t n1, int* l1, int* l2, int64_t* count,
-                  int64_t* vis, int64_t* vos) const {
+  // The shapes the kernel takes: contiguous transforms (unit element strides,
+  // at most one vector loop), or -- group mode, n = 256 x 256 -- the inner
+  // transforms of a larger four-step: inputs one contiguous run of
+  // transforms, outputs of consecutive transforms adjacent (vos 1) with
+  // elements os apart, and at most one more output loop (vos2) over groups of
+  // nt1 transforms.
+  struct L2Shape {
+    int l1, l2, gb;
+    int64_t count, vis, vos, os, nt1, vos2;
+  };
+
+  bool l2fs_shape(const Dim& d, const std::vector<Dim>& V, int64_t n1, L2Shape* sh) const {
     const int lg = log2_exact(d.n), e1 = log2_exact(n1);
-    if (prec || lg < 14 || lg > 22 || e1 < 0 || d.is != 1 || d.os != 1 || V.size() > 1) return false;
+    if (prec || lg < 14 || lg > 22 || e1 < 0 || d.is != 1 || V.size() > 2) return false;
     if (!gb_l2fs_supported(e1, lg - e1)) return false;
-    *l1 = e1;
-    *l2 = lg - e1;
-    *count = V.empty() ? 1 : V[0].n;
-    *vis = V.empty() ? d.n : V[0].is;
-    *vos = V.empty() ? d.n : V[0].os;
-    return *vis > 0 && *vos > 0;
+    *sh = L2Shape{e1, lg - e1, 1, 1, d.n, d.n, 1, 0, 0};
+    if (d.os == 1 && V.size() <= 1) {
+      if (!V.empty()) {
+        sh->count = V[0].n;
+        sh->vis = V[0].is;
+        sh->vos = V[0].os;
+      }
+      return sh->vis > 0 && sh->vos > 0;
+    }
+    const int g = gb_l2fs_group(e1, lg - e1);
+    if (g <= 1 || d.os < 1) return false;
+    int ia = -1;
+    for (int i = 0; i < (int)V.size(); ++i)
+      if (V[i].os == 1 && V[i].is == d.n && V[i].n % g == 0) ia = i;
+    if (ia < 0) return false;
+    sh->gb = g;
+    sh->count = V[ia].n;
+    sh->nt1 = V[ia].n;
+    sh->vos = V[ia].os;  // 1: a group's outputs adjacent
+    sh->os = d.os;
+    if (V.size() == 2) {
+      const Dim& b = V[1 - ia];
+      if (b.is != V[ia].n * d.n || b.os <= 0) return false;
+      sh->count *= b.n;
+      sh->vos2 = b.os;
+    }
+    return true;
   }
 
-  bool l2fs_ring(int l1, int l2, int64_t count, int64_t* S, int64_t* D) const {
+  bool l2fs_ring(const L2Shape& sh, int64_t* S, int64_t* D) const {
     int T1 = 0, T2 = 0;
-    if (!gb_l2fs_tiles(l1, l2, &T1, &T2)) return false;
-    const int64_t n = (int64_t)1 << (l1 + l2);
-    const int64_t per_t = ((int64_t)1 << l2) / T1 + ((int64_t)1 << l1) / T2;  // items per transform
-    int64_t grid = device ? gb_l2fs_grid(l1, l2) : 0;
-    if (grid <= 0) grid = (T1 << l1) <= 4096 ? 304 : 152;
-    int64_t d = std::max<int64_t>(1, (kL2Lag * grid + per_t - 1) / per_t);
+    if (!gb_l2fs_tiles(sh.l1, sh.l2, &T1, &T2)) return false;
+    const int64_t n = (int64_t)1 << (sh.l1 + sh.l2);
+    // items per step of the schedule: the A items of a transform (a group of
+    // gb transforms) and the B items of an earlier one
+    const int64_t nA = ((int64_t)1 << sh.l2) / T1;
+    const int64_t nB = sh.gb > 1 ? ((int64_t)1 << sh.l1) : ((int64_t)1 << sh.l1) / T2;
+    const int64_t per = sh.gb * nA + nB, units = sh.count / sh.gb;
+    int64_t grid = device ? gb_l2fs_grid(sh.l1, sh.l2) : 0;
+    if (grid <= 0) grid = (T1 << sh.l1) <= 4096 ? 304 : 152;
+    int64_t d = std::max<int64_t>(1, (kL2Lag * grid + per - 1) / per);
     int64_t s = 2 * d;
-    const int64_t cap = std::max<int64_t>(1, kL2RingBytes / (n * 8));
+    const int64_t cap = std::max<int64_t>(1, kL2RingBytes / (sh.gb * n * 8));
     if (s > cap) s = cap;
     if (d >= s) d = s - 1;
     if (d < 1) return false;
-    if (d > count) d = count;
-    if (s > count) s = count;
-    *S = s;
-    *D = d;
+    if (d > units) d = units;
+    if (s > units) s = units;
+    *S = s * sh.gb;  // transforms
+    *D = d;          // steps
     return true;
   }
 
   void emit_l2fs(const Dim& d, const std::vector<Dim>& V, int src, int dst, int conj, int64_t n1, int depth) {
-    int l1, l2;
-    int64_t count, vis, vos, S, D;
-    if (!l2fs_shape(d, V, n1, &l1, &l2, &count, &vis, &vos) || !l2fs_ring(l1, l2, count, &S, &D)) {
+    L2Shape sh;
+    int64_t S, D;
+    if (!l2fs_shape(d, V, n1, &sh) || !l2fs_ring(sh, &S, &D)) {
       err = FFT_ERR_WISDOM;
       return;
     }
+    if (sh.gb > 1 && src == dst) {  // a group's outputs interleave with other transforms' inputs
+      err = FFT_ERR_WISDOM;
+      return;
+    }
+    const int l1 = sh.l1, l2 = sh.l2;
+    const int64_t count = sh.count, vis = sh.vis, vos = sh.vos;
     const int64_t n = d.n, n2 = n / n1;
     GbL2FS k{};
     k.logn1 = l1;
@@ -1195,20 +1239,28 @@ struct Builder {
     k.ptwA = A;
     k.ptwB = B;
     k.status = P->d_status;
+    k.gb = sh.gb;
+    k.os = sh.os;
+    k.nt1 = sh.nt1;
+    k.vos2 = sh.vos2;
     const size_t ring = (size_t)S * n * sizeof(float2);
     Step s;
     s.kind = STEP_L2FS;
     s.l2 = k;
     s.src = src;
     s.dst = dst;
-    s.aux = new_scratch(ring + sizeof(unsigned) * gb_l2fs_sync_words(count));
+    s.aux = new_scratch(ring + sizeof(unsigned) * gb_l2fs_sync_words(count, sh.gb));
     P->steps.push_back(s);
     int T1 = 0, T2 = 0;
     gb_l2fs_tiles(l1, l2, &T1, &T2);
     std::ostringstream o;
     o << "pass l2-fourstep n=" << n << " = " << n1 << " x " << n2 << " (eq. 2 in one persistent kernel, "
       << "intermediate in an L2-resident ring of " << S << " transforms, lag " << D << ") T1=" << T1 << " T2=" << T2
-      << " count=" << count << " vis=" << vis << " vos=" << vos << (conj ? " conj" : "");
+      << " count=" << count << " vis=" << vis << " vos=" << vos;
+    if (sh.gb > 1)
+      o << " (B items over one row of " << sh.gb << " transforms; output element stride " << sh.os << ", loops "
+        << sh.nt1 << " x vos " << sh.vos2 << ")";
+    o << (conj ? " conj" : "");
     line(depth, o.str());
   }
 
@@ -1630,15 +1682,17 @@ struct Builder {
     bool l2fs_ok = false, l2fs_busy = false;
     const int64_t l2fs_n1 = lg >= 0 ? ((int64_t)1 << (lg / 2)) : 0;
     {
-      int l1, l2, T1, T2;
-      int64_t cnt, vi, vo, S, D;
+      L2Shape sh;
+      int T1, T2;
+      int64_t S, D;
       // in place: transform t is written only after all its A items have read
-      // it, so equal input and output strides suffice
-      l2fs_ok = lg >= 14 && l2fs_shape(d, V, l2fs_n1, &l1, &l2, &cnt, &vi, &vo) && (!inplace || vi == vo) &&
-                l2fs_ring(l1, l2, cnt, &S, &D);
+      // it, so equal input and output strides suffice (contiguous mode only:
+      // a group's outputs interleave with other transforms' inputs)
+      l2fs_ok = lg >= 14 && l2fs_shape(d, V, l2fs_n1, &sh) &&
+                (!inplace || (sh.gb == 1 && sh.vis == sh.vos)) && l2fs_ring(sh, &S, &D);
       // enough work items to fill the GPU several times over
-      if (l2fs_ok && gb_l2fs_tiles(l1, l2, &T1, &T2))
-        l2fs_busy = cnt * (((int64_t)1 << l2) / T1 + ((int64_t)1 << l1) / T2) >= 8 * 304;
+      if (l2fs_ok && gb_l2fs_tiles(sh.l1, sh.l2, &T1, &T2))
+        l2fs_busy = sh.count * (((int64_t)1 << sh.l2) / T1 + ((int64_t)1 << sh.l1) / T2) >= 8 * 304;
     }
     // estimate mode takes the first candidate: the L2-resident four-step where
     // it beat the two and three TMA passes when measured (2^14..2^21, batches

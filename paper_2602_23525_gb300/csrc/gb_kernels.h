@@ -79,7 +79,8 @@ struct GbL2FS {
   const float2* in;        // set at execute time
   float2* out;
   float2* ring;            // S * n elements (scratch)
-  unsigned* sync;          // [0] item counter, [1 + t] A items done, [1 + count + t] B items done
+  unsigned* sync;          // [0] item counter, [1 + g] A items done, [1 + count / gb + g] B items done,
+                           // g the transform (gb = 1) or group of gb transforms
   int64_t count, vis, vos;
   int64_t S, D;
   int conj;
@@ -89,13 +90,17 @@ struct GbL2FS {
   const float2* ptwB;
   int* status;
   int64_t grid;            // <= 0: one CTA per SM times occupancy
+  int gb;                  // 1, or gb_l2fs_group(): B items over row k1 of gb transforms
+  int64_t os, nt1, vos2;   // gb > 1: output of transform t, element k at
+                           // (t / nt1) vos2 + (t % nt1) vos + k os
 };
 // supported (logn1, logn2) and the tile shape: transforms' columns / rows per item
 int gb_l2fs_supported(int logn1, int logn2);
 int gb_l2fs_tiles(int logn1, int logn2, int* T1, int* T2);
 // persistent CTAs the launch uses on the current device (for the lag D)
 int gb_l2fs_grid(int logn1, int logn2);
-size_t gb_l2fs_sync_words(int64_t count);  // unsigned words of k.sync
+size_t gb_l2fs_sync_words(int64_t count, int gb);  // unsigned words of k.sync
+int gb_l2fs_group(int logn1, int logn2);  // transforms per B item in group mode (0: not built)
 cudaError_t gb_launch_l2fs(const GbL2FS& k, cudaStream_t st);
 
 // Single-pass transforms of n = 2^13 .. 2^17 spread over a thread-block

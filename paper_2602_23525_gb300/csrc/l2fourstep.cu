@@ -190,8 +190,14 @@ struct L2FSCfg {
 //   publisher warp: after done[b], hands buffer b back (pub[b]) and publishes
 //     the item to the other CTAs (a gpu-scope fence, then the count).
 // CONJ: the backward transform (inputs and outputs conjugated), a template
-// argument so that the forward kernel carries no conjugation code
-template <int L1, int L2, int TP, int MINB, int CONJ>
+// argument so that the forward kernel carries no conjugation code.
+// GB > 1: a B item takes row k1 of GB consecutive transforms (a group) and
+// stores its outputs k = k1 + k2 n1 of transform t at out + off(t) + k os,
+// off(t) = (t / nt1) vos2 + (t % nt1) vos: with vos = 1 the GB transforms'
+// outputs are adjacent, so strided outputs (the inner transforms of a larger
+// four-step, whose outputs interleave) still store whole 128-byte runs.  The
+// schedule then runs in groups of GB transforms.
+template <int L1, int L2, int TP, int MINB, int CONJ, int GB = 1>
 __global__ void __launch_bounds__(TP / 16 + 64, MINB)
     gb_l2fs_kernel(const __grid_constant__ GbL2FS k, const __grid_constant__ CUtensorMap tm, int tmap_ok, int pos) {
   using CA = P2<L1>;
@@ -206,8 +212,10 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
   float2* twa = ibuf + NB * BUFE;        // stage tables of the n1-point DFTs
   float2* twb = twa + CA::twoff(CA::NST);  // and of the n2-point DFTs
   const int tid = threadIdx.x;
-  const int64_t nA = N2 / T1, nB = N1 / T2;
-  const int64_t total = k.count * (nA + nB);
+  static_assert(GB == 1 || GB == T2, "a group fills the tile's rows");
+  const int64_t NG = k.count / GB;  // groups (transforms when GB = 1)
+  const int64_t nA = N2 / T1, nB = GB > 1 ? (int64_t)N1 : N1 / T2;  // A items per transform, B per group
+  const int64_t total = NG * (GB * nA + nB);
 
   if (tid == 0) {
     for (int b = 0; b < NB; ++b) {
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
   __syncthreads();
   unsigned* ctr = k.sync;
   unsigned* doneA = k.sync + 1;
-  unsigned* doneB = k.sync + 1 + k.count;
+  unsigned* doneB = k.sync + 1 + NG;
 
   if (tid >= NT + 32) {
     // ---------------------------------------------------------------- publisher warp
@@ -247,7 +255,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       if (lane == 0) {
         mbar_arrive(smem_addr(bars + 2 * NB + b));
         __threadfence();
-        atomicAdd((r.kind == 0 ? doneA : doneB) + r.t, 1u);
+        atomicAdd(r.kind == 0 ? doneA + r.t / GB : doneB + r.t, 1u);
       }
       __syncwarp();
     }
@@ -287,13 +295,18 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       idx = __shfl_sync(0xffffffffu, idx, 0);
       ItemSlot r{0, 0, -1, 0};
       if (idx < total) {
-        const ItemRef d = decode(idx, k.count, k.D, nA, nB);
-        r = ItemSlot{d.t, d.j, d.kind, (int)(d.t % k.S)};
+        const ItemRef d = decode(idx, NG, k.D, GB * nA, nB);
+        if (d.kind == 0) {
+          const int64_t t = d.t * GB + d.j / nA;  // d.t: the group
+          r = ItemSlot{t, d.j % nA, 0, (int)(t % k.S)};
+        } else {
+          r = ItemSlot{d.t, d.j, d.kind, GB == 1 ? (int)(d.t % k.S) : 0};  // GB > 1: t is the group
+        }
       }
       int ok = 1;
       if (lane == 0) {
-        if (r.kind == 1) ok = wait_count(doneA + r.t, (unsigned)nA);
-        else if (r.kind == 0 && r.t >= k.S) ok = wait_count(doneB + (r.t - k.S), (unsigned)nB);
+        if (r.kind == 1) ok = wait_count(doneA + r.t, (unsigned)(GB * nA));
+        else if (r.kind == 0 && r.t >= k.S) ok = wait_count(doneB + (r.t - k.S) / GB, (unsigned)nB);
         info[b] = r;
       }
       if (!__shfl_sync(0xffffffffu, ok, 0)) {
@@ -318,7 +331,15 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
             // above made visible to this thread, and the proxy fence to its
             // bulk copy
             asm volatile("fence.proxy.async.global;" ::: "memory");
-            bulk_copy(smem_addr(dst), k.ring + (int64_t)r.slot * N + r.j * T2 * N2, (uint32_t)(TP * 8), full);
+            if constexpr (GB == 1) {
+              bulk_copy(smem_addr(dst), k.ring + (int64_t)r.slot * N + r.j * T2 * N2, (uint32_t)(TP * 8), full);
+            } else {
+              // row k1 = j of each transform of the group (S is a multiple of GB)
+              const int64_t s0 = (r.t * GB) % k.S;
+#pragma unroll 1
+              for (int q = 0; q < GB; ++q)
+                bulk_copy(smem_addr(dst + q * N2), k.ring + (s0 + q) * N + r.j * N2, (uint32_t)(N2 * 8), full);
+            }
           }
         } else {
           mbar_arrive(full);
@@ -386,9 +407,18 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       stage_out_x<L2, 0>(v, xbuf + bj * CB::PITCH, buj);
       gb_bar<NT>();
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      item_stages<L2, 1, false, NT>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH,
-                                    k.out + r.t * k.vos + row0 + bt, N1, twb, buj, bu, CONJ,
-                                    make_float2(0.f, 0.f), z4, z4);
+      float2* gout;
+      int64_t ostr;
+      if constexpr (GB == 1) {
+        gout = k.out + r.t * k.vos + row0 + bt;
+        ostr = N1;
+      } else {
+        const int t = (int)(r.t * GB) + bt, nt1 = (int)k.nt1;
+        gout = k.out + (int64_t)(t / nt1) * k.vos2 + (int64_t)(t % nt1) * k.vos + r.j * k.os;
+        ostr = (int64_t)N1 * k.os;
+      }
+      item_stages<L2, 1, false, NT>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH, gout, ostr, twb, buj, bu,
+                                    CONJ, make_float2(0.f, 0.f), z4, z4);
     }
     mbar_arrive(smem_addr(bars + NB + b));  // this thread's stores are done
   }
@@ -420,7 +450,7 @@ cudaError_t launch(const GbL2FS& k, cudaStream_t st) {
   int64_t grid = k.grid > 0 ? k.grid : grid_of<L1, L2>();
   if (grid < 1) return cudaErrorInvalidConfiguration;
   if (grid > items) grid = items;
-  cudaError_t e = cudaMemsetAsync(k.sync, 0, sizeof(unsigned) * gb_l2fs_sync_words(k.count), st);
+  cudaError_t e = cudaMemsetAsync(k.sync, 0, sizeof(unsigned) * gb_l2fs_sync_words(k.count, k.gb), st);
   if (e != cudaSuccess) return e;
   // the input's tensor map: dims (n2 columns, n1 rows, count transforms)
   GbP2 g{};
@@ -437,16 +467,24 @@ cudaError_t launch(const GbL2FS& k, cudaStream_t st) {
   memset(&tm, 0, sizeof(tm));
   int pos = 0;
   const int tmap_ok = gb_p2_rows_map(g, G::T1, &tm, &pos);
-  if (k.conj) {
-    auto fb = gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 1>;
-    if (cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem) != cudaSuccess)
+  auto go = [&](auto fn) -> cudaError_t {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem) != cudaSuccess)
       return cudaGetLastError();
-    fb<<<(unsigned)grid, G::TP / 16 + 64, G::smem, st>>>(k, tm, tmap_ok, pos);
-  } else {
-    gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 0><<<(unsigned)grid, G::TP / 16 + 64, G::smem, st>>>(k, tm, tmap_ok,
-                                                                                            pos);
+    fn<<<(unsigned)grid, G::TP / 16 + 64, G::smem, st>>>(k, tm, tmap_ok, pos);
+    return cudaGetLastError();
+  };
+  if (k.gb > 1) {
+    // groups of 16 transforms: built for n = 256 x 256 (the inner transforms
+    // of 2^22..2^24-point four-steps)
+    if constexpr (L1 == 8 && L2 == 8) {
+      if (k.gb != G::T2 || k.count % k.gb || k.S % k.gb || k.nt1 % k.gb) return cudaErrorInvalidValue;
+      return k.conj ? go(gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 1, G::T2>)
+                    : go(gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 0, G::T2>);
+    } else {
+      return cudaErrorInvalidValue;
+    }
   }
-  return cudaGetLastError();
+  return k.conj ? go(gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 1>) : go(gb_l2fs_kernel<L1, L2, G::TP, G::MINB, 0>);
 }
 
 #define GB_L2FS_CASES(X) X(7, 7) X(7, 8) X(8, 8) X(8, 9) X(9, 9) X(9, 10) X(10, 10) X(10, 11) X(11, 11)
@@ -479,7 +517,9 @@ int gb_l2fs_grid(int logn1, int logn2) {
   return 0;
 }
 
-size_t gb_l2fs_sync_words(int64_t count) { return (size_t)(1 + 2 * count); }
+size_t gb_l2fs_sync_words(int64_t count, int gb) { return (size_t)(1 + 2 * (count / (gb > 1 ? gb : 1))); }
+
+int gb_l2fs_group(int logn1, int logn2) { return logn1 == 8 && logn2 == 8 ? L2FSCfg<8, 8>::T2 : 0; }
 
 cudaError_t gb_launch_l2fs(const GbL2FS& k, cudaStream_t st) {
 #define GB_L2FS_L(a, b) if (k.logn1 == a && k.logn2 == b) return launch<a, b>(k, st);

@@ -122,12 +122,27 @@ def test_plan_mixed_radix():
 
 
 def test_plan_large_is_multi_pass():
-    """Radix-sqrt(n) steps (sec. 3.3): 2^24 = 256 x 65536, the 65536-point rows
-    again split 256 x 256 -- three passes, each a one-CTA TMA pass kernel."""
+    """Radix-sqrt(n) steps (sec. 3.3): 2^24 = 256 x 65536, the 256-point column
+    pass with its twiddle, then the 65536 rows as 256 x 256 in the L2-resident
+    four-step, its B items over one row of 16 transforms (their outputs
+    interleave 256 apart); with wisdom for the rows' sub-problem, three one-CTA
+    TMA passes as before."""
     t = explain([(2 ** 24, 1, 1)])
     assert "cooley-tukey n=16777216 = 256 x 65536" in t
+    assert t.count("pass p2-tma") == 1 and "post-twiddle" in t
+    assert "pass l2-fourstep n=65536 = 256 x 256" in t and "one row of 16 transforms" in t, t
+    assert "output element stride 256" in t, t
+    for e, n1 in ((22, 64), (23, 128)):
+        t = explain([(2 ** e, 1, 1)], [(2 ** (26 - e), 2 ** e, 2 ** e)])
+        assert f"= {n1} x 65536" in t and "one row of 16 transforms" in t, t
+    gbfft.fft_forget_wisdom()
+    gbfft.fft_import_wisdom("gbfft-wisdom 1\nr1 n=65536 is=1 os=256 v=[(256,65536,1)] ip=0\tsplit:256\n")
+    try:
+        t = explain([(2 ** 24, 1, 1)])
+    finally:
+        gbfft.fft_forget_wisdom()
     assert "cooley-tukey n=65536 = 256 x 256" in t
-    assert t.count("pass p2-tma") == 3
+    assert t.count("pass p2-tma") == 3, t
     assert t.count("post-twiddle") >= 2
     t = explain([(2 ** 20, 1, 1)], [(4, 2 ** 20, 2 ** 20)])
     assert "= 1024 x 1024" in t and t.count("pass p2-tma") == 2
@@ -244,7 +259,8 @@ def test_plan_l2_resident_four_step():
         txt = explain([(n, 1, 1)], [(2 ** 26 // n, n, n)])
         assert f"pass l2-fourstep n={n} = {2 ** (e // 2)} x {n >> (e // 2)}" in txt, txt
         assert txt.count("pass ") == 1, txt
-    assert "l2-fourstep" not in explain([(2 ** 22, 1, 1)], [(16, 2 ** 22, 2 ** 22)])
+    # 2^22 takes a 64-point column pass and its 65536-point rows in groups, not one 2048 x 2048 kernel
+    assert "pass l2-fourstep n=4194304" not in explain([(2 ** 22, 1, 1)], [(16, 2 ** 22, 2 ** 22)])
     assert "l2-fourstep" not in explain([(65536, 1, 1)], [(8, 65536, 65536)])
     assert "l2-fourstep" not in explain([(65536, 1024, 1024)], [(1024, 1, 1)])
 

@@ -103,3 +103,44 @@ def test_full_size_measured_plan_sampled(e):
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 2e-6, (v, err)
     plan.destroy()
+
+
+@pytest.mark.parametrize("e,b", [(22, 2), (23, 1), (24, 1)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_group_mode_inner_transforms(e, b, sign):
+    """2^22..2^24 as n1 x 65536 (eq. (2)): the n1-point column pass, then the
+    65536-point rows in the L2-resident four-step whose B items take one row
+    of 16 transforms and store their outputs n1 apart (group mode), against
+    the FP64 oracle on every transform."""
+    n = 1 << e
+    how = [(b, n, n)] if b > 1 else []
+    x = fft_inputs.uniform_c64(n * b, fft_inputs.seed_for(8, e + b))
+    err, info = check([(n, 1, 1)], how, sign, x, flags=gbfft.FFT_ESTIMATE, algo="ct")
+    assert f"= {1 << (e - 16)} x 65536" in info and "one row of 16 transforms" in info, info
+
+
+def test_group_mode_padded_batch_and_full_size_sampled():
+    """A padded batch stride (the column pass writes the rows contiguously, so
+    the group kernel sees the same layout) and 2^24 x 4 at full size with the
+    measured plan, on sampled transforms."""
+    n, b = 1 << 22, 3
+    how = [(b, n + 8, n + 16)]
+    x = fft_inputs.uniform_c64((n + 8) * b, fft_inputs.seed_for(8, 40))
+    err, info = check([(n, 1, 1)], how, -1, x, flags=gbfft.FFT_ESTIMATE, algo="ct")
+    assert "one row of 16 transforms" in info, info
+    n, b = 1 << 24, 4
+    x = fft_inputs.uniform_c64(n * b, fft_inputs.seed_for(8, 41))
+    xin = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xin)
+    gbfft.fft_forget_wisdom()
+    plan = gbfft.Plan([(n, 1, 1)], [(b, n, n)], 1, gbfft.FFT_MEASURE)
+    for _ in range(2):
+        plan.execute(xin, y)
+    assert gbfft.fft_sync_status(plan.handle) == gbfft.FFT_OK
+    print(plan.info)
+    yh = y.cpu().numpy()
+    for v in (0, b - 1):
+        ref = oracle.dft(x[v * n:(v + 1) * n], [(n, 1, 1)], [], 1, algo="ct")
+        got = yh[v * n:(v + 1) * n].astype(np.complex128)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-6, v
+    plan.destroy()

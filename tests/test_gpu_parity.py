@@ -419,6 +419,23 @@ def test_mr_kernel_contiguous(n, sign):
         assert "pass mr-tma" in info, info
 
 
+@pytest.mark.parametrize("n,sched", [(1000, "R=8.5.5.5"), (2187, "R=9.9.9.3"), (3125, "R=5.5.5.5.5"),
+                                     (3600, "R=16.9.5.5"), (3840, "R=16.16.3.5"), (7168, "R=16.16.4.7")])
+def test_mr_compile_time_schedules(n, sched):
+    """The lengths with a compile-time radix schedule (stockham_mrc.cu): both
+    signs, contiguous batches with a ragged tile, and strided columns through
+    tensor-map boxes (load=rows)."""
+    b = max(3, 12000 // n) | 1
+    for sign in (-1, 1):
+        x = u(n * b, 760 + n)
+        err, info = check([(n, 1, 1)], [(b, n, n)], sign, x, flags=EST)
+        assert "pass mr-tma" in info and sched in info, info
+    cols = 16
+    x = u(n * cols, 770 + n)
+    err, info = check([(n, cols, 1)], [(cols, 1, n)], -1, x, flags=EST)
+    assert "pass mr-tma" in info and "load=rows" in info, info
+
+
 def test_mr_kernel_layouts():
     """Strided columns (tensor-map boxes, several boxes of 256 rows and a partial
     one), non-adjacent transforms (one copy each / plain loads for odd n), an
