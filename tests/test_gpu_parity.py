@@ -424,7 +424,8 @@ def test_mr_kernel_contiguous(n, sign):
 def test_mr_compile_time_schedules(n, sched):
     """The lengths with a compile-time radix schedule (stockham_mrc.cu): both
     signs, contiguous batches with a ragged tile, and strided columns through
-    tensor-map boxes (load=rows)."""
+    tensor-map boxes (load=rows) where two transforms fit one CTA (3600 and
+    7168 need 400 and 448 threads each: the generic pass takes their columns)."""
     b = max(3, 12000 // n) | 1
     for sign in (-1, 1):
         x = u(n * b, 760 + n)
@@ -433,7 +434,8 @@ def test_mr_compile_time_schedules(n, sched):
     cols = 16
     x = u(n * cols, 770 + n)
     err, info = check([(n, cols, 1)], [(cols, 1, n)], -1, x, flags=EST)
-    assert "pass mr-tma" in info and "load=rows" in info, info
+    if n not in (3600, 7168):
+        assert "pass mr-tma" in info and "load=rows" in info, info
 
 
 def test_mr_kernel_layouts():
