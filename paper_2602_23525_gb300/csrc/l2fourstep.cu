@@ -298,9 +298,9 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
         const ItemRef d = decode(idx, NG, k.D, GB * nA, nB);
         if (d.kind == 0) {
           const int64_t t = d.t * GB + d.j / nA;  // d.t: the group
-          r = ItemSlot{t, d.j % nA, 0, (int)(t % k.S)};
+          r = ItemSlot{t, d.j % nA, 0, (int)(GB == 1 ? t % k.S : d.t % (k.S / GB))};
         } else {
-          r = ItemSlot{d.t, d.j, d.kind, GB == 1 ? (int)(d.t % k.S) : 0};  // GB > 1: t is the group
+          r = ItemSlot{d.t, d.j, d.kind, (int)(d.t % (k.S / GB))};  // GB > 1: t is the group
         }
       }
       int ok = 1;
@@ -334,11 +334,9 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
             if constexpr (GB == 1) {
               bulk_copy(smem_addr(dst), k.ring + (int64_t)r.slot * N + r.j * T2 * N2, (uint32_t)(TP * 8), full);
             } else {
-              // row k1 = j of each transform of the group (S is a multiple of GB)
-              const int64_t s0 = (r.t * GB) % k.S;
-#pragma unroll 1
-              for (int q = 0; q < GB; ++q)
-                bulk_copy(smem_addr(dst + q * N2), k.ring + (s0 + q) * N + r.j * N2, (uint32_t)(N2 * 8), full);
+              // row k1 = j of the group's transforms: adjacent in the group's
+              // slot ([k1][transform][l2], as the A items store it)
+              bulk_copy(smem_addr(dst), k.ring + (int64_t)r.slot * GB * N + r.j * GB * N2, (uint32_t)(TP * 8), full);
             }
           }
         } else {
@@ -385,7 +383,9 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
     if (r.kind < 0) break;
     float2* xbuf = ibuf + b * BUFE;  // the item's tile, then its exchange rows
     const float2* tile = xbuf;
-    float2* slot = k.ring + (int64_t)r.slot * N;
+    // the item's transform in the ring: slot [k1][l2] (GB = 1), or its rows
+    // interleaved with the group's other transforms, [k1][t mod GB][l2]
+    float2* slot = GB == 1 ? k.ring + (int64_t)r.slot * N : k.ring + (int64_t)r.slot * GB * N + (r.t % GB) * N2;
     if (r.kind == 0) {
       // ---- A(t, j): columns [j T1, (j+1) T1) of transform t into the slot
       const int64_t col = r.j * T1 + at;  // l2
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       gb_bar<NT>();  // the tile is read: its buffer takes the exchange rows
       stage_out_x<L1, 0>(v, xbuf + at * CA::PITCH, au);
       gb_bar<NT>();
-      item_stages<L1, 1, true, NT>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, N2, twa, auj, au,
+      item_stages<L1, 1, true, NT>(v, xbuf + aj * CA::PITCH, xbuf + at * CA::PITCH, slot + col, GB * N2, twa, auj, au,
                                    CONJ, pa, pb0, pb1);
     } else {
       // ---- B(t, j): rows [j T2, (j+1) T2) of the slot into Y[k1 + k2 n1]
