@@ -186,7 +186,7 @@ struct L2FSCfg {
 //     L2; B: one bulk copy of the ring rows, from L2) and arrives on full[b];
 //   compute warps: wait on full[b], compute the item's stages (named barrier
 //     1 among themselves) with buffer b as the exchange rows once the tile is
-//     read, store, arrive on done[b];
+//     read, store, arrive on done[b] (one arrival per warp);
 //   publisher warp: after done[b], hands buffer b back (pub[b]) and publishes
 //     the item to the other CTAs (a gpu-scope fence, then the count).
 // CONJ: the backward transform (inputs and outputs conjugated), a template
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       // full: one arrival per producer lane (lane 0's with the expected bytes
       // of the bulk copies) plus lane 0's release of info[b]
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(33));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + NB + b)), "r"(NT));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + NB + b)), "r"(NT / 32));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + 2 * NB + b)), "r"(1));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -420,7 +420,10 @@ __global__ void __launch_bounds__(TP / 16 + 64, MINB)
       item_stages<L2, 1, false, NT>(v, xbuf + bj * CB::PITCH, xbuf + bt * CB::PITCH, gout, ostr, twb, buj, bu,
                                     CONJ, make_float2(0.f, 0.f), z4, z4);
     }
-    mbar_arrive(smem_addr(bars + NB + b));  // this thread's stores are done
+    // the warp's stores are done: one arrival per warp, after a warp barrier
+    // that orders the other lanes' stores before lane 0's (release) arrival
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(smem_addr(bars + NB + b));
   }
 }
 
