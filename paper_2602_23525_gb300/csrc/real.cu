@@ -37,28 +37,44 @@ __device__ __forceinline__ void real_offsets(const GbRealIO& r, int64_t v, int64
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// pairs (k, m - k), k = 0 .. m/2, of transform v
+// pairs (k, m - k), k = 0 .. m/2, of transform v, in place.  A thread takes
+// U pairs at once (k, k + blockDim, ...): all their loads before any store,
+// so that U round trips to memory overlap instead of following each other
+// (the pairs are distinct, but the compiler cannot know that the stores of
+// one pair do not alias the loads of the next).
 __global__ void gb_r2c_post_kernel(const GbRealIO r, float2* z) {
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = 4;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * U;
   const int64_t pairs = r.m / 2 + 1;
   for (int64_t v = blockIdx.y; v < r.count; v += gridDim.y) {
     int64_t io, oo;
     real_offsets(r, v, &io, &oo);
     float2* y = z + oo;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < pairs; k += step) {
-      const int64_t kk = r.m - k;
-      const float2 a = y[k * r.os];
-      const float2 b = kk == r.m ? a : y[kk * r.os];  // Z[m] = Z[0]
-      const float2 bc = conjf2(b);
-      const float2 ze = make_float2(0.5f * (a.x + bc.x), 0.5f * (a.y + bc.y));
-      // (a - conj b) / (2i) = -i (a - conj b) / 2
-      const float2 d = make_float2(a.x - bc.x, a.y - bc.y);
-      const float2 zo = make_float2(0.5f * d.y, -0.5f * d.x);
-      const float2 t = gb_pw_cmul(__ldg(r.tw + k), zo);
-      const float2 xk = make_float2(ze.x + t.x, ze.y + t.y);
-      const float2 xm = make_float2(ze.x - t.x, -(ze.y - t.y));
-      y[k * r.os] = xk;
-      if (kk != k) y[kk * r.os] = xm;
+    for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x; k0 < pairs; k0 += step) {
+      float2 a[U], b[U], w[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + (int64_t)u * blockDim.x, kk = r.m - k;
+        if (k < pairs) {
+          a[u] = y[k * r.os];
+          b[u] = kk == r.m ? a[u] : y[kk * r.os];  // Z[m] = Z[0]
+          w[u] = __ldg(r.tw + k);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + (int64_t)u * blockDim.x, kk = r.m - k;
+        if (k < pairs) {
+          const float2 bc = conjf2(b[u]);
+          const float2 ze = make_float2(0.5f * (a[u].x + bc.x), 0.5f * (a[u].y + bc.y));
+          // (a - conj b) / (2i) = -i (a - conj b) / 2
+          const float2 d = make_float2(a[u].x - bc.x, a[u].y - bc.y);
+          const float2 zo = make_float2(0.5f * d.y, -0.5f * d.x);
+          const float2 t = gb_pw_cmul(w[u], zo);
+          y[k * r.os] = make_float2(ze.x + t.x, ze.y + t.y);
+          if (kk != k) y[kk * r.os] = make_float2(ze.x - t.x, -(ze.y - t.y));
+        }
+      }
     }
   }
 }
@@ -75,24 +91,40 @@ __global__ void gb_r2c_promote_kernel(const GbRealIO r, const float* x, float2* 
   }
 }
 
+// U entries a thread, all loads before the stores (as in the r2c step)
 __global__ void gb_c2r_pre_kernel(const GbRealIO r, const float2* X, float2* w) {
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = 4;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * U;
   for (int64_t v = blockIdx.y; v < r.count; v += gridDim.y) {
     int64_t io, oo;
     real_offsets(r, v, &io, &oo);
     const float2* xi = X + io;
     float2* wo = w + v * r.m;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < r.m; k += step) {
-      float2 a = __ldg(xi + k * r.is);
-      float2 b = conjf2(__ldg(xi + (r.m - k) * r.is));
-      if (k == 0) {  // X[0] and X[m] are self-conjugate: their real parts
-        a.y = 0.f;
-        b.y = 0.f;
+    for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x; k0 < r.m; k0 += step) {
+      float2 a[U], b[U], tw[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + (int64_t)u * blockDim.x;
+        if (k < r.m) {
+          a[u] = __ldg(xi + k * r.is);
+          b[u] = conjf2(__ldg(xi + (r.m - k) * r.is));
+          tw[u] = __ldg(r.tw + k);
+        }
       }
-      const float2 s = make_float2(a.x + b.x, a.y + b.y);
-      const float2 d = make_float2(a.x - b.x, a.y - b.y);
-      const float2 t = gb_pw_cmul(conjf2(__ldg(r.tw + k)), d);  // w_n^{-k} (a - b)
-      wo[k] = make_float2(s.x - t.y, s.y + t.x);                 // s + i t
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + (int64_t)u * blockDim.x;
+        if (k < r.m) {
+          if (k == 0) {  // X[0] and X[m] are self-conjugate: their real parts
+            a[u].y = 0.f;
+            b[u].y = 0.f;
+          }
+          const float2 s = make_float2(a[u].x + b[u].x, a[u].y + b[u].y);
+          const float2 d = make_float2(a[u].x - b[u].x, a[u].y - b[u].y);
+          const float2 t = gb_pw_cmul(conjf2(tw[u]), d);  // w_n^{-k} (a - b)
+          wo[k] = make_float2(s.x - t.y, s.y + t.x);      // s + i t
+        }
+      }
     }
   }
 }
