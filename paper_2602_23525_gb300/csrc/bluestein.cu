@@ -19,32 +19,63 @@ namespace {
 // one transform along x, so that the offsets of a transform are computed once
 // per thread and the entry index needs no 64-bit division (the group
 // executor uses the per-element forms of gb_pointwise.cuh instead).
+// The pointwise steps take U entries a thread, all loads before the stores,
+// so that a thread's round trips to memory overlap (the compiler cannot tell
+// that a store does not alias the next entry's loads).
+constexpr int kU = 4;
+
 __global__ void gb_blue_pre_kernel(const GbBlueIO b) {
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * kU;
   for (int64_t v = blockIdx.y; v < b.count; v += gridDim.y) {
     int64_t io, oo;
     gb_pw_offsets(b, v, &io, &oo);
     const float2* x = b.in + io;
     float2* a = b.work + v * b.m;
-    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < b.m; l += step) {
-      float2 val = make_float2(0.f, 0.f);
-      if (l < b.n) {
-        float2 xv = __ldg(x + l * b.is);
-        if (b.conj) xv.y = -xv.y;
-        val = gb_pw_cmul(xv, __ldg(b.w + l));
+    for (int64_t l0 = (int64_t)blockIdx.x * blockDim.x * kU + threadIdx.x; l0 < b.m; l0 += step) {
+      float2 xv[kU], wv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t l = l0 + (int64_t)u * blockDim.x;
+        xv[u] = wv[u] = make_float2(0.f, 0.f);
+        if (l < b.n) {
+          xv[u] = __ldg(x + l * b.is);
+          wv[u] = __ldg(b.w + l);
+        }
       }
-      a[l] = val;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t l = l0 + (int64_t)u * blockDim.x;
+        if (l < b.m) {
+          if (b.conj) xv[u].y = -xv[u].y;
+          a[l] = gb_pw_cmul(xv[u], wv[u]);  // zero beyond n
+        }
+      }
     }
   }
 }
 
 __global__ void gb_blue_mul_kernel(const GbBlueIO b, float2* data) {
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * kU;
   for (int64_t v = blockIdx.y; v < b.count; v += gridDim.y) {
     float2* z = data + v * b.m;
-    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < b.m; l += step) {
-      const float2 p = gb_pw_cmul(__ldcg(z + l), __ldg(b.B + l));
-      z[l] = make_float2(p.x, -p.y);
+    for (int64_t l0 = (int64_t)blockIdx.x * blockDim.x * kU + threadIdx.x; l0 < b.m; l0 += step) {
+      float2 zv[kU], bv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t l = l0 + (int64_t)u * blockDim.x;
+        if (l < b.m) {
+          zv[u] = __ldcg(z + l);
+          bv[u] = __ldg(b.B + l);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t l = l0 + (int64_t)u * blockDim.x;
+        if (l < b.m) {
+          const float2 p = gb_pw_cmul(zv[u], bv[u]);
+          z[l] = make_float2(p.x, -p.y);
+        }
+      }
     }
   }
 }
