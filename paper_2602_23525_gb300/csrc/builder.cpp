@@ -1190,7 +1190,7 @@ struct Builder {
     // items per step of the schedule: the A items of a transform (a group of
     // gb transforms) and the B items of an earlier one
     const int64_t nA = ((int64_t)1 << sh.l2) / T1;
-    const int64_t nB = sh.gb > 1 ? ((int64_t)1 << sh.l1) : ((int64_t)1 << sh.l1) / T2;
+    const int64_t nB = ((int64_t)1 << sh.l1) * sh.gb / T2;  // B items per transform or group
     const int64_t per = sh.gb * nA + nB, units = sh.count / sh.gb;
     int64_t grid = device ? gb_l2fs_grid(sh.l1, sh.l2) : 0;
     if (grid <= 0) grid = (T1 << sh.l1) <= 4096 ? 304 : 152;
@@ -1258,8 +1258,8 @@ struct Builder {
       << "intermediate in an L2-resident ring of " << S << " transforms, lag " << D << ") T1=" << T1 << " T2=" << T2
       << " count=" << count << " vis=" << vis << " vos=" << vos;
     if (sh.gb > 1)
-      o << " (B items over one row of " << sh.gb << " transforms; output element stride " << sh.os << ", loops "
-        << sh.nt1 << " x vos " << sh.vos2 << ")";
+      o << " (B items over " << T2 / sh.gb << " rows of " << sh.gb << " transforms; output element stride " << sh.os
+        << ", loops " << sh.nt1 << " x vos " << sh.vos2 << ")";
     o << (conj ? " conj" : "");
     line(depth, o.str());
   }

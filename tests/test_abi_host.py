@@ -124,17 +124,17 @@ def test_plan_mixed_radix():
 def test_plan_large_is_multi_pass():
     """Radix-sqrt(n) steps (sec. 3.3): 2^24 = 256 x 65536, the 256-point column
     pass with its twiddle, then the 65536 rows as 256 x 256 in the L2-resident
-    four-step, its B items over one row of 16 transforms (their outputs
+    four-step, its B items over two rows of 8 transforms (their outputs
     interleave 256 apart); with wisdom for the rows' sub-problem, three one-CTA
     TMA passes as before."""
     t = explain([(2 ** 24, 1, 1)])
     assert "cooley-tukey n=16777216 = 256 x 65536" in t
     assert t.count("pass p2-tma") == 1 and "post-twiddle" in t
-    assert "pass l2-fourstep n=65536 = 256 x 256" in t and "one row of 16 transforms" in t, t
+    assert "pass l2-fourstep n=65536 = 256 x 256" in t and "B items over 2 rows of 8 transforms" in t, t
     assert "output element stride 256" in t, t
     for e, n1 in ((22, 64), (23, 128)):
         t = explain([(2 ** e, 1, 1)], [(2 ** (26 - e), 2 ** e, 2 ** e)])
-        assert f"= {n1} x 65536" in t and "one row of 16 transforms" in t, t
+        assert f"= {n1} x 65536" in t and "B items over 2 rows of 8 transforms" in t, t
     gbfft.fft_forget_wisdom()
     gbfft.fft_import_wisdom("gbfft-wisdom 1\nr1 n=65536 is=1 os=256 v=[(256,65536,1)] ip=0\tsplit:256\n")
     try:

@@ -110,13 +110,14 @@ def test_full_size_measured_plan_sampled(e):
 def test_group_mode_inner_transforms(e, b, sign):
     """2^22..2^24 as n1 x 65536 (eq. (2)): the n1-point column pass, then the
     65536-point rows in the L2-resident four-step whose B items take one row
-    of 16 transforms and store their outputs n1 apart (group mode), against
+    of 8 transforms, two rows each, and store their outputs n1 apart (group
+    mode), against
     the FP64 oracle on every transform."""
     n = 1 << e
     how = [(b, n, n)] if b > 1 else []
     x = fft_inputs.uniform_c64(n * b, fft_inputs.seed_for(8, e + b))
     err, info = check([(n, 1, 1)], how, sign, x, flags=gbfft.FFT_ESTIMATE, algo="ct")
-    assert f"= {1 << (e - 16)} x 65536" in info and "one row of 16 transforms" in info, info
+    assert f"= {1 << (e - 16)} x 65536" in info and "B items over 2 rows of 8 transforms" in info, info
 
 
 def test_group_mode_padded_batch_and_full_size_sampled():
@@ -127,7 +128,7 @@ def test_group_mode_padded_batch_and_full_size_sampled():
     how = [(b, n + 8, n + 16)]
     x = fft_inputs.uniform_c64((n + 8) * b, fft_inputs.seed_for(8, 40))
     err, info = check([(n, 1, 1)], how, -1, x, flags=gbfft.FFT_ESTIMATE, algo="ct")
-    assert "one row of 16 transforms" in info, info
+    assert "B items over 2 rows of 8 transforms" in info, info
     n, b = 1 << 24, 4
     x = fft_inputs.uniform_c64(n * b, fft_inputs.seed_for(8, 41))
     xin = torch.from_numpy(x).cuda()
